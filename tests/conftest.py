@@ -1,0 +1,22 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line(
+        "markers", "gpu: needs a GB300 GPU and the CUDA library (run with -m gpu)")
+    config.addinivalue_line("markers", "slow: long statistical test")
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _build_cpu_helpers():
+    import oracle
+    import workloads
+    oracle.build()
+    workloads.build()
