@@ -1,0 +1,231 @@
+/*
+ * susp.h -- C ABI of the GB300 library that advances the minimal
+ * dense-suspension model of Li, Royer & Ness (arXiv 2307.13802):
+ * spheres under contact forces with Coulomb-capped tangential history
+ * (Sec. II.A, Eqs. 3-4), one-body Stokes drag (Sec. II.B, Eqs. 5-6),
+ * regularised pairwise lubrication (Sec. II.B, Eqs. 8-18), one-body and
+ * pairwise Brownian forces tied to those resistances (Sec. II.C,
+ * Eqs. 19-24), integrated by Velocity-Verlet (Sec. II, Eqs. 1-2) in a
+ * tilted periodic box sheared at a fixed rate with the strain flip of
+ * Sec. II.E, and reporting the pair-virial stress (Sec. II.A, II.B, II.D).
+ *
+ * Conventions used by every call:
+ *   - Particles are identified by their tag = index in the caller's arrays.
+ *     For a batch of R replicas the tags of replica r are offset_r + local
+ *     index, offset_r = sum of the sizes of the replicas before r.
+ *   - Vectors are passed as row-major arrays of shape [count][3] (x, y, z).
+ *     Host pointers are read or written in tag order whatever order the
+ *     library keeps internally.
+ *   - Flow x, gradient y, vorticity z; the imposed flow is
+ *     U_inf = rate (y - Ly/2) x, Omega_inf = -(rate/2) z.  The box is
+ *     [0,Lx) x [0,Ly) x [0,Lz) in the sliding-brick form of the tilted box:
+ *     the image above in y is shifted by tilt = strain * Ly in x.
+ *   - The force on sphere i from sphere j (i the lower tag, n the unit vector
+ *     from i to j) is applied to i and its negative to j; the stress is
+ *     sigma = (1/V) sum_pairs F_{i<-j} (x) r_ij (tension positive).
+ *   - All calls are synchronous with respect to the host unless stated.
+ *     One handle must not be used by two host threads at once.
+ *   - Every call returns SUSP_OK or an error code; after an error the handle
+ *     stays valid and susp_last_error() gives a message.  No call throws.
+ *
+ * Ownership: input arrays are copied before the call returns; the library
+ * owns its device memory (allocated through the hook of
+ * susp_set_allocator() if one is set, else cudaMalloc) and frees it in
+ * susp_destroy().  Output arrays are caller-owned and must hold the stated
+ * number of elements.
+ */
+#ifndef SUSP_H
+#define SUSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SUSP_OK 0
+#define SUSP_EINVAL 1    /* invalid argument (NULL, N <= 0, radius <= 0,    */
+                         /* box < 3 list cutoffs, dt <= 0, kT < 0, mu < 0)  */
+#define SUSP_ENOMEM 2    /* device or host allocation failed                */
+#define SUSP_ECUDA 3     /* a CUDA runtime call failed                      */
+#define SUSP_ESTATE 4    /* call order (e.g. step before set_state)         */
+#define SUSP_ENEIGH 5    /* neighbour row exceeded its capacity             */
+#define SUSP_EUNSTABLE 6 /* non-finite position/velocity or runaway overlap */
+#define SUSP_ETIMEOUT 7  /* a bounded device wait gave up                   */
+#define SUSP_ENODEV 8    /* no CUDA device is visible                       */
+
+/* ---- parameters --------------------------------------------------------- */
+#define SUSP_FP64 0  /* every step in double precision                      */
+#define SUSP_MIXED 1 /* pair arithmetic in single precision on gaps formed  */
+                     /* from double positions; integration, tangential      */
+                     /* history and stress accumulation in double           */
+
+typedef struct susp_params {
+  double eta;         /* liquid viscosity                                   */
+  double rho;         /* particle density; m = 4/3 pi rho a^3, I = 2/5 m a^2 */
+  double kn;          /* normal contact stiffness (Eq. 3)                   */
+  double kt;          /* tangential stiffness (Eq. 3); used when mu > 0      */
+  double mu;          /* static friction coefficient, 0 = frictionless       */
+  double xi_min;      /* regularised gap xi_eff (paper: 1e-3)               */
+  double xi_max;      /* lubrication cutoff on xi (paper: 0.05)             */
+  double skin;        /* neighbour-list skin, length units                  */
+  double shear_rate;  /* batch handles: this replica's shear rate           */
+  double kT;          /* batch handles: this replica's thermal energy       */
+  double torque_sign; /* sign of the chi term of T_ji in Eq. 24; -1 makes    */
+                      /* the pair noise covariance (2kT/dt) R exactly        */
+  double dt;          /* timestep used by susp_evaluate() before any step;  */
+                      /* each susp_step*() call replaces it with its own dt */
+  uint64_t seed;      /* batch handles: this replica's Philox key           */
+  int32_t precision;  /* SUSP_FP64 or SUSP_MIXED                            */
+  int32_t noise;      /* 1: Brownian terms on                               */
+  int32_t lubrication;/* 1: lubrication and pair noise on                   */
+  int32_t onebody;    /* 1: one-body drag and noise on                      */
+  int32_t contact;    /* 1: contact forces on                               */
+  int32_t sample_every;/* accumulate the stress every this many steps (>=1) */
+  int32_t kmax;       /* neighbour row capacity (0: default 48)             */
+  int32_t threads_per_particle; /* 0 = autotune, else 1, 2, 4 or 8          */
+  int32_t use_graphs; /* 1: replay steps as CUDA graphs (default)           */
+  int32_t reserved[3];
+} susp_params;
+
+/* Fills *p with the defaults: eta = rho = 1, kn = 1e4, kt = 0, mu = 0,
+ * xi_min = 1e-3, xi_max = 0.05, skin = 0.3, shear_rate = 1, kT = 0,
+ * torque_sign = -1, dt = 1e-4, seed = 0, FP64, all terms on, sample_every = 1,
+ * kmax = 48, autotuned threads per particle, graphs on. */
+void susp_default_params(susp_params* p);
+
+typedef struct susp_s susp_t;
+
+/* ---- lifetime ----------------------------------------------------------- */
+/* One system of N spheres with the given radii (N doubles, all > 0) in the
+ * box [0,box[0]) x [0,box[1]) x [0,box[2]) with tilt 0.  Each box edge must
+ * be at least three neighbour-list cutoffs, 3 * (2 a_max (1 + xi_max/2) +
+ * skin).  Selects device 0 (or the current device).  Nothing is allocated on
+ * the device until susp_set_state(). */
+int susp_create(susp_t** out, int64_t N, const double* radii,
+                const double box[3], const susp_params* p);
+
+/* R independent replicas stepped together (Sec. II.E: ensembles of 10-800
+ * realisations).  N_r[R] sizes, radii[sum N_r], boxes[R][3], p_r[R]
+ * parameters (eta, rho, kn, kt, mu, shear_rate, kT, seed may differ per
+ * replica; xi_min, xi_max, skin, precision and the switches are taken from
+ * p_r[0]). */
+int susp_create_batch(susp_t** out, int32_t R, const int64_t* N_r,
+                      const double* radii, const double* boxes,
+                      const susp_params* p_r);
+
+/* Frees all device and host memory of the handle.  NULL is a no-op. */
+void susp_destroy(susp_t* h);
+
+/* Message of the last failing call on this handle ("" if none).  The string
+ * is owned by the handle and valid until its next call. */
+const char* susp_last_error(const susp_t* h);
+
+/* Message of the last susp_create*() failure in this thread. */
+const char* susp_create_error(void);
+
+/* ---- plumbing ----------------------------------------------------------- */
+/* Work is issued on this cudaStream_t; NULL selects the handle's own
+ * non-blocking stream (the default).  The legacy default stream cannot be
+ * captured into graphs, so pass a created stream.  Takes effect for later
+ * calls; captured graphs are rebuilt. */
+int susp_set_stream(susp_t* h, void* cuda_stream);
+
+/* Device memory comes from alloc(bytes, ctx) and is returned with
+ * free(ptr, ctx).  Must be called before the first susp_set_state(). */
+int susp_set_allocator(susp_t* h, void* (*alloc)(size_t, void*),
+                       void (*release)(void*, void*), void* ctx);
+
+/* ---- state -------------------------------------------------------------- */
+/* Positions x[N][3] (wrapped into the box), velocities U[N][3] and angular
+ * velocities Omega[N][3] from HOST memory; U or Omega NULL means zero.
+ * Forces are re-evaluated (without advancing time) before the next step. */
+int susp_set_state(susp_t* h, const double* x, const double* U,
+                   const double* Omega);
+
+/* Same, from DEVICE memory of the handle's device (e.g. tensors). */
+int susp_set_state_device(susp_t* h, const double* x, const double* U,
+                          const double* Omega);
+
+/* Sets the evaluation counter k used as the noise counter (the forces held
+ * after a step of index n have k = n + 1; setup forces have the k in
+ * effect) and the strain of replica `replica` (-1: all), within
+ * (-Lx/(2Ly), Lx/(2Ly)].  Forces are re-evaluated before the next step. */
+int susp_set_clock(susp_t* h, int64_t k, int32_t replica, double strain);
+
+/* Copies positions, velocities and angular velocities to HOST arrays
+ * [N][3] in tag order; any pointer may be NULL. */
+int susp_get_state(susp_t* h, double* x, double* U, double* Omega);
+
+/* Forces F[N][3] and torques T[N][3] of the last evaluation, tag order. */
+int susp_get_forces(susp_t* h, double* F, double* T);
+
+/* ---- the method ----------------------------------------------------------- */
+/* Cell binning by a counting sort on the cell key, then the skin-padded
+ * half neighbour list: every unordered pair with
+ * |r|^2 < ((a_i + a_j)(1 + xi_max/2) + skin)^2 (cutoff xi <= xi_max of
+ * Sec. II.B plus the skin of Sec. II), stored once; the tangential history
+ * of touching pairs is carried over.  Done automatically by the step when
+ * the displacement bound exceeds the skin. */
+int susp_build_neighbors(susp_t* h);
+
+/* Evaluates forces, torques and pair stresses at the current state without
+ * advancing time (tangential history is not incremented). */
+int susp_evaluate(susp_t* h);
+
+/* Advances n_steps Velocity-Verlet steps of a single-replica handle with the
+ * given shear rate, thermal energy, timestep and Philox seed (Sec. II,
+ * Eqs. 1-24, Sec. II.E).  Returns SUSP_EUNSTABLE on non-finite state and
+ * SUSP_ENEIGH if a neighbour row overflowed. */
+int susp_step(susp_t* h, int64_t n_steps, double shear_rate, double kT,
+              double dt, uint64_t seed);
+
+/* Advances every replica of a batch handle n_steps steps of size dt with the
+ * per-replica rate, kT and seed given at creation. */
+int susp_step_batch(susp_t* h, int64_t n_steps, double dt);
+
+/* Stress of replica `replica` averaged over the sampled evaluations since
+ * the previous call (which it resets).  out[SUSP_STRESS_LEN]:
+ *   [ 0.. 8] contact        sigma^C  (row-major 3x3, Sec. II.A)
+ *   [ 9..17] lubrication    sigma^HL (Sec. II.B)
+ *   [18..26] pair Brownian  sigma^BL (Sec. II.D, averages to zero)
+ *   [27..35] drag stresslet (20/3) pi eta sum a^3 E / V (Sec. II.B)
+ *   [36..44] kinetic        sum m (U - U_inf)(U - U_inf) / V (full steps)
+ *   [45..53] rotational kinetic sum I (W - W_inf)(W - W_inf) / V
+ *   [54] eta_r = (sigma^C + sigma^HL + drag)_xy / (eta rate)   (Sec. II.E)
+ *   [55] N1 = sigma_xx - sigma_yy, [56] N2 = sigma_yy - sigma_zz of that sum
+ *   [57] number of sampled evaluations */
+#define SUSP_STRESS_LEN 58
+int susp_stress(susp_t* h, int32_t replica, double* out);
+
+/* The current half neighbour list as tag pairs ij[count][2] with i < j in
+ * lexicographic order; *count receives the number of pairs, at most cap are
+ * written (cap = 0 only counts). */
+int susp_get_pairs(susp_t* h, int32_t* ij, int64_t cap, int64_t* count);
+
+/* Touching pairs carrying tangential history: ij[count][2] (i < j, sorted)
+ * and xi_t[count][3]; as susp_get_pairs for cap and count. */
+int susp_get_history(susp_t* h, int32_t* ij, double* xi_t, int64_t cap,
+                     int64_t* count);
+
+/* Diagnostics, info[SUSP_INFO_LEN]: [0] k, [1] neighbour builds so far,
+ * [2] longest row at the last build, [3] row capacity, [4] pairs in the
+ * list, [5] strain of replica 0, [6] tilt of replica 0, [7] threads per
+ * particle in use, [8] precision, [9] replicas, [10] total spheres,
+ * [11] steps replayed through graphs, [12] device bytes held. */
+#define SUSP_INFO_LEN 13
+int susp_get_info(susp_t* h, double* info);
+
+/* ---- checkpoint ------------------------------------------------------------- */
+/* Writes / reads positions, velocities, forces, tangential history, k,
+ * strains and the step counters; resuming reproduces the run it was taken
+ * from (counter-based noise carries no generator state). */
+int susp_save(susp_t* h, const char* path);
+int susp_load(susp_t* h, const char* path);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SUSP_H */

@@ -1,0 +1,957 @@
+// api.cu -- host runtime behind the C ABI of include/susp.h: parameter
+// validation, device memory, the per-step launch sequence (eager or replayed
+// as CUDA graphs with a conditional node for the neighbour rebuild), stress
+// bookkeeping and checkpoints.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/susp.h"
+#include "susp_internal.h"
+
+using namespace susp;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct GraphChunk {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace
+
+struct susp_s {
+  int dev = 0;
+  int R = 1;
+  int64_t N = 0, Npad = 0;
+  std::vector<int64_t> Nr, off;
+  std::vector<double> radii, mass, inertia;
+  std::vector<int> rep_of;
+  std::vector<Replica> repl_h;
+  std::vector<susp_params> pr;
+  susp_params p0{};
+  int kmax = 48;
+  int tpp = 1;
+  double rcmax = 0.0;
+  double amax = 0.0;
+  int64_t ncell = 0;
+  // block map (host + device)
+  std::vector<int> bm_rep, bm_start, bm_end, rep_bstart;
+  BlockMap bm{};
+  // device
+  bool allocated = false;
+  Arrays A{};
+  double* d_radius = nullptr;
+  double* d_mass = nullptr;
+  double* d_inertia = nullptr;
+  int* d_rep_of = nullptr;
+  double* d_stage = nullptr;      // [3][N][3] staging for host state
+  cudaStream_t stream = nullptr;
+  void* (*ualloc)(size_t, void*) = nullptr;
+  void (*ufree)(void*, void*) = nullptr;
+  void* uctx = nullptr;
+  std::vector<void*> blocks;
+  size_t bytes = 0;
+  // run state
+  bool forces_valid = false;
+  bool have_state = false;
+  int64_t steps_done = 0;
+  double last_dt = -1.0;
+  double cur_rate = NAN, cur_kT = NAN;
+  uint64_t cur_seed = 0;
+  bool seed_set = false;
+  int64_t graph_steps = 0;
+  std::map<int64_t, GraphChunk> graphs;
+  cudaStream_t side = nullptr;
+  cudaStream_t own_stream = nullptr;
+  std::string err;
+  std::string graph_err;
+};
+
+namespace {
+
+int fail(susp_t* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+#define CK(call)                                                          \
+  do {                                                                    \
+    cudaError_t e_ = (call);                                              \
+    if (e_ != cudaSuccess)                                                \
+      return fail(h, SUSP_ECUDA, std::string(#call) + ": " +             \
+                                     cudaGetErrorString(e_));            \
+  } while (0)
+
+const double kPi = 3.14159265358979323846;
+
+void fill_replica_physics(Replica& R, const susp_params& p) {
+  R.rate = p.shear_rate;
+  R.kT = p.kT;
+  R.eta = p.eta;
+  R.kn = p.kn;
+  R.kt = p.kt;
+  R.mu = p.mu;
+  R.key0 = (uint32_t)(p.seed & 0xffffffffull);
+  R.key1 = (uint32_t)(p.seed >> 32);
+}
+
+int validate_params(const susp_params* p, std::string& msg) {
+  if (!(p->eta > 0)) { msg = "eta must be > 0"; return SUSP_EINVAL; }
+  if (!(p->rho > 0)) { msg = "rho must be > 0"; return SUSP_EINVAL; }
+  if (!(p->kn >= 0)) { msg = "kn must be >= 0"; return SUSP_EINVAL; }
+  if (!(p->kt >= 0)) { msg = "kt must be >= 0"; return SUSP_EINVAL; }
+  if (!(p->mu >= 0)) { msg = "mu must be >= 0"; return SUSP_EINVAL; }
+  if (!(p->xi_min > 0) || !(p->xi_max >= p->xi_min)) {
+    msg = "need 0 < xi_min <= xi_max"; return SUSP_EINVAL;
+  }
+  if (!(p->skin >= 0)) { msg = "skin must be >= 0"; return SUSP_EINVAL; }
+  if (!(p->kT >= 0)) { msg = "kT must be >= 0"; return SUSP_EINVAL; }
+  if (!(p->dt > 0) || !std::isfinite(p->dt)) { msg = "dt must be > 0"; return SUSP_EINVAL; }
+  if (!std::isfinite(p->shear_rate)) { msg = "shear rate must be finite"; return SUSP_EINVAL; }
+  if (p->precision != SUSP_FP64 && p->precision != SUSP_MIXED) {
+    msg = "precision must be SUSP_FP64 or SUSP_MIXED"; return SUSP_EINVAL;
+  }
+  if (p->sample_every < 1) { msg = "sample_every must be >= 1"; return SUSP_EINVAL; }
+  if (p->kmax < 0 || p->kmax > 64) { msg = "kmax must be in [0, 64]"; return SUSP_EINVAL; }
+  const int t = p->threads_per_particle;
+  if (!(t == 0 || t == 1 || t == 2 || t == 4 || t == 8)) {
+    msg = "threads_per_particle must be 0, 1, 2, 4 or 8"; return SUSP_EINVAL;
+  }
+  return SUSP_OK;
+}
+
+int common_create(susp_t** out, int32_t R, const int64_t* N_r,
+                  const double* radii, const double* boxes,
+                  const susp_params* p_r) {
+  g_create_error.clear();
+  if (!out) { g_create_error = "out is NULL"; return SUSP_EINVAL; }
+  *out = nullptr;
+  if (R <= 0 || !N_r || !radii || !boxes || !p_r) {
+    g_create_error = "invalid arguments (R <= 0 or NULL pointer)";
+    return SUSP_EINVAL;
+  }
+  std::string msg;
+  for (int r = 0; r < R; ++r) {
+    int rc = validate_params(&p_r[r], msg);
+    if (rc) { g_create_error = "replica " + std::to_string(r) + ": " + msg; return rc; }
+    if (N_r[r] <= 0) { g_create_error = "every replica needs N > 0"; return SUSP_EINVAL; }
+  }
+  int64_t N = 0;
+  for (int r = 0; r < R; ++r) N += N_r[r];
+  if (N >= (int64_t)1 << 31) { g_create_error = "too many spheres"; return SUSP_EINVAL; }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    g_create_error = "no CUDA device";
+    return SUSP_ENODEV;
+  }
+  susp_t* h = new (std::nothrow) susp_s();
+  if (!h) { g_create_error = "out of host memory"; return SUSP_ENOMEM; }
+  cudaGetDevice(&h->dev);
+  h->R = R;
+  h->N = N;
+  h->Npad = (N + 31) / 32 * 32;
+  h->p0 = p_r[0];
+  h->pr.assign(p_r, p_r + R);
+  h->last_dt = p_r[0].dt;
+  h->kmax = p_r[0].kmax > 0 ? p_r[0].kmax : 48;
+  h->tpp = p_r[0].threads_per_particle > 0 ? p_r[0].threads_per_particle : 1;
+  h->Nr.assign(N_r, N_r + R);
+  h->off.resize(R + 1);
+  h->off[0] = 0;
+  for (int r = 0; r < R; ++r) h->off[r + 1] = h->off[r] + N_r[r];
+  h->radii.assign(radii, radii + N);
+  h->mass.resize(N);
+  h->inertia.resize(N);
+  h->rep_of.resize(N);
+  for (int r = 0; r < R; ++r) {
+    const double cm = 4.0 / 3.0 * kPi * p_r[r].rho;
+    for (int64_t i = h->off[r]; i < h->off[r + 1]; ++i) {
+      const double a = radii[i];
+      if (!(a > 0) || !std::isfinite(a)) {
+        delete h;
+        g_create_error = "radii must be finite and > 0";
+        return SUSP_EINVAL;
+      }
+      h->amax = std::max(h->amax, a);
+      h->mass[i] = cm * a * a * a;
+      h->inertia[i] = 0.4 * h->mass[i] * a * a;
+      h->rep_of[i] = r;
+    }
+  }
+  const double xi_max = p_r[0].xi_max;
+  h->rcmax = (h->amax + h->amax) * (1.0 + 0.5 * xi_max);
+  const double rlist = h->rcmax + p_r[0].skin;
+  const double guard = rlist * (1.0 + 1e-9) + 1e-12;
+  h->repl_h.resize(R);
+  int64_t cell_base = 0;
+  for (int r = 0; r < R; ++r) {
+    Replica& Rr = h->repl_h[r];
+    std::memset(&Rr, 0, sizeof(Rr));
+    for (int d = 0; d < 3; ++d) Rr.L[d] = boxes[3 * r + d];
+    if (!(Rr.L[0] > 0 && Rr.L[1] > 0 && Rr.L[2] > 0)) {
+      delete h;
+      g_create_error = "box edges must be > 0";
+      return SUSP_EINVAL;
+    }
+    fill_replica_physics(Rr, p_r[r]);
+    Rr.V = Rr.L[0] * Rr.L[1] * Rr.L[2];
+    Rr.flip_at = 0.5 * Rr.L[0] / Rr.L[1];
+    Rr.flip_by = Rr.L[0] / Rr.L[1];
+    Rr.strain = 0.0;
+    Rr.tilt = 0.0;
+    // cell thickness along x for the largest tilt Lx/2
+    const double tmax = 0.5 * Rr.L[0];
+    const double wx = Rr.L[0] * Rr.L[1] / std::sqrt(Rr.L[1] * Rr.L[1] + tmax * tmax);
+    Rr.nc[0] = (int)std::floor(wx / guard);
+    Rr.nc[1] = (int)std::floor(Rr.L[1] / guard);
+    Rr.nc[2] = (int)std::floor(Rr.L[2] / guard);
+    if (Rr.nc[0] < 3 || Rr.nc[1] < 3 || Rr.nc[2] < 3) {
+      delete h;
+      char buf[256];
+      std::snprintf(buf, sizeof buf,
+                    "replica %d: box (%g, %g, %g) holds fewer than 3 cells of the "
+                    "list cutoff %g along some axis", r, Rr.L[0], Rr.L[1], Rr.L[2], rlist);
+      g_create_error = buf;
+      return SUSP_EINVAL;
+    }
+    for (int d = 0; d < 3; ++d) Rr.hcell[d] = 1.0 / Rr.nc[d];
+    Rr.cell_base = cell_base;
+    cell_base += (int64_t)Rr.nc[0] * Rr.nc[1] * Rr.nc[2];
+    Rr.p0 = h->off[r];
+    Rr.n = N_r[r];
+  }
+  h->ncell = cell_base;
+  // block map: blocks never straddle replicas
+  h->rep_bstart.push_back(0);
+  for (int r = 0; r < R; ++r) {
+    for (int64_t s = h->off[r]; s < h->off[r + 1]; s += kBlock) {
+      h->bm_rep.push_back(r);
+      h->bm_start.push_back((int)s);
+      h->bm_end.push_back((int)std::min<int64_t>(s + kBlock, h->off[r + 1]));
+    }
+    h->rep_bstart.push_back((int)h->bm_rep.size());
+  }
+  *out = h;
+  return SUSP_OK;
+}
+
+void* dev_alloc(susp_t* h, size_t bytes) {
+  bytes = (bytes + 255) / 256 * 256;
+  void* p = nullptr;
+  if (h->ualloc) {
+    p = h->ualloc(bytes, h->uctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (p) {
+    h->blocks.push_back(p);
+    h->bytes += bytes;
+    cudaMemsetAsync(p, 0, bytes, h->stream);
+  }
+  return p;
+}
+
+void release_all(susp_t* h) {
+  for (auto& kv : h->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  h->graphs.clear();
+  for (void* p : h->blocks) {
+    if (h->ufree) h->ufree(p, h->uctx);
+    else cudaFree(p);
+  }
+  h->blocks.clear();
+  h->bytes = 0;
+  h->allocated = false;
+  if (h->side) { cudaStreamDestroy(h->side); h->side = nullptr; }
+}
+
+template <typename T>
+bool alloc_n(susp_t* h, T** p, int64_t n) {
+  *p = (T*)dev_alloc(h, sizeof(T) * (size_t)std::max<int64_t>(n, 1));
+  return *p != nullptr;
+}
+
+int allocate(susp_t* h) {
+  if (h->allocated) return SUSP_OK;
+  CK(cudaSetDevice(h->dev));
+  if (!h->stream) {
+    if (!h->own_stream) CK(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+    h->stream = h->own_stream;
+  }
+  Arrays& A = h->A;
+  A.N = h->N;
+  A.Npad = h->Npad;
+  A.kmax = h->kmax;
+  A.R = h->R;
+  A.ncell = h->ncell;
+  const int64_t Np = h->Npad;
+  const bool fric = true;  // history arrays are cheap to hold; used when mu > 0
+  bool ok = true;
+  for (int c = 0; c < 2; ++c) {
+    ok &= alloc_n(h, &A.pos.a[c], Np);
+    ok &= alloc_n(h, &A.vel.a[c], Np);
+    ok &= alloc_n(h, &A.omg.a[c], Np);
+    ok &= alloc_n(h, &A.frc.a[c], 3 * Np);
+    ok &= alloc_n(h, &A.trq.a[c], 3 * Np);
+    ok &= alloc_n(h, &A.tag.a[c], Np);
+    ok &= alloc_n(h, &A.rep.a[c], Np);
+    ok &= alloc_n(h, &A.nbr.a[c], (int64_t)h->kmax * Np);
+    ok &= alloc_n(h, &A.nnb.a[c], Np);
+    ok &= alloc_n(h, &A.cmsk.a[c], Np);
+    if (fric) ok &= alloc_n(h, &A.hist.a[c], 3 * (int64_t)h->kmax * Np);
+  }
+  ok &= alloc_n(h, &A.slot_of_tag, Np);
+  ok &= alloc_n(h, &A.cell, Np);
+  ok &= alloc_n(h, &A.key, Np);
+  ok &= alloc_n(h, &A.perm, Np);
+  ok &= alloc_n(h, &A.cell_count, h->ncell + 1);
+  ok &= alloc_n(h, &A.cell_start, h->ncell + 1);
+  ok &= alloc_n(h, &A.cell_fill, h->ncell + 1);
+  const int64_t nparts = (h->ncell + kBlock * 8 - 1) / (kBlock * 8);
+  ok &= alloc_n(h, &A.scan_part, nparts + 1);
+  const int nb = (int)h->bm_rep.size();
+  ok &= alloc_n(h, &A.pair_partial, (int64_t)nb * kPartialLen);
+  ok &= alloc_n(h, &A.kin_partial, (int64_t)nb * kKinLen);
+  ok &= alloc_n(h, &A.stress_acc, (int64_t)h->R * 48);
+  ok &= alloc_n(h, &A.rep_bstart, h->R + 1);
+  ok &= alloc_n(h, &A.repl, h->R);
+  ok &= alloc_n(h, &A.ctl, 1);
+  if (h->p0.precision == SUSP_MIXED) {
+    ok &= alloc_n(h, &A.posm, Np);
+    ok &= alloc_n(h, &A.velm, Np);
+    ok &= alloc_n(h, &A.omgm, Np);
+  }
+  int *brep = nullptr, *bst = nullptr, *ben = nullptr;
+  ok &= alloc_n(h, &brep, nb);
+  ok &= alloc_n(h, &bst, nb);
+  ok &= alloc_n(h, &ben, nb);
+  ok &= alloc_n(h, &h->d_radius, h->N);
+  ok &= alloc_n(h, &h->d_mass, h->N);
+  ok &= alloc_n(h, &h->d_inertia, h->N);
+  ok &= alloc_n(h, &h->d_rep_of, h->N);
+  ok &= alloc_n(h, &h->d_stage, 9 * h->N);
+  if (!ok) {
+    release_all(h);
+    return fail(h, SUSP_ENOMEM, "device allocation failed");
+  }
+  cudaStream_t st = h->stream;
+  CK(cudaMemcpyAsync(brep, h->bm_rep.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(bst, h->bm_start.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ben, h->bm_end.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(A.rep_bstart, h->rep_bstart.data(), sizeof(int) * (h->R + 1),
+                     cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->d_radius, h->radii.data(), sizeof(double) * h->N, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->d_mass, h->mass.data(), sizeof(double) * h->N, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->d_inertia, h->inertia.data(), sizeof(double) * h->N, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(h->d_rep_of, h->rep_of.data(), sizeof(int) * h->N, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(A.repl, h->repl_h.data(), sizeof(Replica) * h->R, cudaMemcpyHostToDevice, st));
+  Ctl c{};
+  c.need_rebuild = 1;
+  CK(cudaMemcpyAsync(A.ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  h->bm.rep = brep;
+  h->bm.start = bst;
+  h->bm.end = ben;
+  h->bm.nblocks = nb;
+  h->allocated = true;
+  return SUSP_OK;
+}
+
+StepArgs make_args(const susp_t* h, double dt, int advance, int sample) {
+  StepArgs s{};
+  const susp_params& p = h->p0;
+  s.dt = dt;
+  s.hdt = 0.5 * dt;
+  s.xi_min = p.xi_min;
+  s.xi_max = p.xi_max;
+  s.skin = p.skin;
+  s.rcmax = h->rcmax;
+  double rm = 0.0;
+  for (const Replica& R : h->repl_h) rm = std::max(rm, std::fabs(R.rate));
+  s.rate_max = rm;
+  s.torque_sign = p.torque_sign;
+  s.noise = p.noise;
+  s.lubrication = p.lubrication;
+  s.onebody = p.onebody;
+  s.contact = p.contact;
+  int fric = 0;
+  for (const Replica& R : h->repl_h) fric |= (R.mu > 0.0 && R.kt > 0.0);
+  s.friction = fric;
+  s.advance = advance;
+  s.sample = sample;
+  return s;
+}
+
+// Pull the device-side strain/tilt into the host table (they evolve on the
+// device), refresh the per-call physics and push the table back.
+int sync_replicas(susp_t* h, double dt) {
+  std::vector<Replica> dev(h->R);
+  CK(cudaMemcpyAsync(dev.data(), h->A.repl, sizeof(Replica) * h->R,
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int r = 0; r < h->R; ++r) {
+    Replica& R = h->repl_h[r];
+    R.strain = dev[r].strain;
+    R.tilt = dev[r].tilt;
+    R.rate_dt = R.rate * dt;
+    R.noise_c = std::sqrt(2.0 * R.kT / dt);
+  }
+  CK(cudaMemcpyAsync(h->A.repl, h->repl_h.data(), sizeof(Replica) * h->R,
+                     cudaMemcpyHostToDevice, h->stream));
+  return SUSP_OK;
+}
+
+void drop_graphs(susp_t* h) {
+  for (auto& kv : h->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+  }
+  h->graphs.clear();
+}
+
+int check_errors(susp_t* h) {
+  Ctl c{};
+  CK(cudaMemcpyAsync(&c, h->A.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaGetLastError());
+  if (c.err) {
+    int e = c.err;
+    int zero = 0;
+    cudaMemcpyAsync(&h->A.ctl->err, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream);
+    cudaStreamSynchronize(h->stream);
+    if (e & kErrOverflow) {
+      char buf[160];
+      std::snprintf(buf, sizeof buf,
+                    "a neighbour row held %d pairs, above the capacity kmax = %d", c.max_row,
+                    h->kmax);
+      return fail(h, SUSP_ENEIGH, buf);
+    }
+    if (e & (kErrNonFinite | kErrWrap)) return fail(h, SUSP_EUNSTABLE, "non-finite positions or velocities");
+    return fail(h, SUSP_EUNSTABLE, "unstable state");
+  }
+  return SUSP_OK;
+}
+
+void launch_integrate(susp_t* h, const StepArgs& s, int close, int sample_kin,
+                      unsigned long long cond, int use_cond, cudaStream_t st) {
+  if (h->p0.precision == SUSP_MIXED)
+    launch_integrate_mixed(h->A, h->bm, s, close, sample_kin, st, cond, use_cond);
+  else
+    launch_integrate_fp64(h->A, h->bm, s, close, sample_kin, st, cond, use_cond);
+}
+
+void launch_pair(susp_t* h, const StepArgs& s, cudaStream_t st) {
+  if (h->p0.precision == SUSP_MIXED) {
+    launch_pair_mixed(h->A, h->bm, s, h->tpp, st);
+  } else {
+    launch_pair_fp64(h->A, h->bm, s, h->tpp, st);
+  }
+}
+
+void launch_finalize(susp_t* h, const StepArgs& s, int sample_kin, cudaStream_t st) {
+  if (h->p0.precision == SUSP_MIXED)
+    launch_finalize_mixed(h->A, h->bm, s, sample_kin, st);
+  else
+    launch_finalize_fp64(h->A, h->bm, s, sample_kin, st);
+}
+
+// Setup evaluation (time not advanced): rebuild if due, clear, evaluate.
+void enqueue_setup_eval(susp_t* h, double dt, int sample, cudaStream_t st) {
+  StepArgs s = make_args(h, dt, 0, sample);
+  launch_rebuild(h->A, h->bm, s, st, h->p0.precision == SUSP_MIXED);
+  if (h->p0.precision == SUSP_MIXED) launch_mirror(h->A, h->bm, st);
+  launch_zero_forces(h->A, st);
+  launch_pair(h, s, st);
+  launch_reduce_stress(h->A, h->bm, sample, 0, st);
+}
+
+bool sampled(const susp_t* h, int64_t step_index) {
+  return (step_index % h->p0.sample_every) == 0;
+}
+
+// Enqueue steps [first, first + n) of the run: each step is the fused
+// kick/drift, the (gated) rebuild, the force evaluation and the stress
+// reduction; the chunk ends with the closing half kick.
+void enqueue_steps(susp_t* h, int64_t first, int64_t n, double dt,
+                   cudaStream_t st, bool capture, std::vector<unsigned long long>* conds) {
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t step = first + i;
+    const int close = i > 0 ? 1 : 0;
+    const int skin_prev = close && sampled(h, step - 1);
+    const int samp = sampled(h, step);
+    StepArgs s = make_args(h, dt, 1, samp);
+    unsigned long long cond = 0;
+    if (capture) {
+      cudaStreamCaptureStatus cs;
+      cudaGraph_t g;
+      cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+      cudaGraphConditionalHandle hd;
+      cudaGraphConditionalHandleCreate(&hd, g, 0, 0);
+      cond = (unsigned long long)hd;
+      conds->push_back(cond);
+    }
+    launch_integrate(h, s, close, skin_prev, cond, capture ? 1 : 0, st);
+    if (capture) {
+      cudaStreamCaptureStatus cs;
+      cudaGraph_t g;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      cudaStreamGetCaptureInfo(st, &cs, nullptr, &g, &deps, nullptr, &nd);
+      cudaGraphNodeParams np{};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = (cudaGraphConditionalHandle)cond;
+      np.conditional.type = cudaGraphCondTypeIf;
+      np.conditional.size = 1;
+      cudaGraphNode_t node;
+      cudaGraphAddNode(&node, g, deps, nullptr, nd, &np);
+      cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      cudaStreamBeginCaptureToGraph(h->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+      launch_rebuild(h->A, h->bm, s, h->side, h->p0.precision == SUSP_MIXED);
+      cudaStreamEndCapture(h->side, &body);
+    } else {
+      launch_rebuild(h->A, h->bm, s, st, h->p0.precision == SUSP_MIXED);
+    }
+    launch_pair(h, s, st);
+    launch_reduce_stress(h->A, h->bm, samp, skin_prev, st);
+  }
+  StepArgs s = make_args(h, dt, 1, 0);
+  const int last_kin = sampled(h, first + n - 1);
+  launch_finalize(h, s, last_kin, st);
+  launch_reduce_stress(h->A, h->bm, 0, last_kin, st);
+}
+
+int get_graph(susp_t* h, int64_t n, double dt, GraphChunk** out) {
+  auto it = h->graphs.find(n);
+  if (it != h->graphs.end()) { *out = &it->second; return SUSP_OK; }
+  if (!h->side) CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+  GraphChunk gc;
+  std::vector<unsigned long long> conds;
+  CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  enqueue_steps(h, 0, n, dt, h->stream, true, &conds);
+  cudaError_t e = cudaStreamEndCapture(h->stream, &gc.graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, SUSP_ECUDA, std::string("graph capture failed: ") + cudaGetErrorString(e));
+  }
+  e = cudaGraphInstantiate(&gc.exec, gc.graph, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(gc.graph);
+    return fail(h, SUSP_ECUDA, std::string("graph instantiation failed: ") + cudaGetErrorString(e));
+  }
+  h->graphs[n] = gc;
+  *out = &h->graphs[n];
+  return SUSP_OK;
+}
+
+int run_steps(susp_t* h, int64_t n_steps, double dt) {
+  if (!h->have_state) return fail(h, SUSP_ESTATE, "susp_set_state() must come first");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(h, SUSP_EINVAL, "dt must be > 0");
+  if (n_steps < 0) return fail(h, SUSP_EINVAL, "n_steps must be >= 0");
+  CK(cudaSetDevice(h->dev));
+  if (dt != h->last_dt) drop_graphs(h);
+  int rc = sync_replicas(h, dt);
+  if (rc) return rc;
+  h->last_dt = dt;
+  cudaStream_t st = h->stream;
+  if (!h->forces_valid) {
+    enqueue_setup_eval(h, dt, 0, st);
+    h->forces_valid = true;
+  }
+  const int64_t chunk = 32;
+  int64_t done = 0;
+  while (done < n_steps) {
+    const int64_t left = n_steps - done;
+    const bool graphs_ok = h->p0.use_graphs && (chunk % h->p0.sample_every == 0);
+    if (graphs_ok && left >= chunk && (h->steps_done % h->p0.sample_every) == 0) {
+      GraphChunk* g = nullptr;
+      rc = get_graph(h, chunk, dt, &g);
+      if (rc) {
+        // capture is unavailable: remember why and launch eagerly from now on
+        h->graph_err = h->err;
+        h->err.clear();
+        h->p0.use_graphs = 0;
+        continue;
+      }
+      CK(cudaGraphLaunch(g->exec, st));
+      done += chunk;
+      h->steps_done += chunk;
+      h->graph_steps += chunk;
+    } else {
+      enqueue_steps(h, h->steps_done, left, dt, st, false, nullptr);
+      done += left;
+      h->steps_done += left;
+    }
+  }
+  return check_errors(h);
+}
+
+int gather_host(susp_t* h, int what, double* out) {
+  if (!out) return SUSP_OK;
+  launch_gather(h->A, what, h->d_stage, h->stream);
+  CK(cudaMemcpyAsync(out, h->d_stage, sizeof(double) * 3 * h->N, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SUSP_OK;
+}
+
+int list_pairs(susp_t* h, int with_history, int32_t* ij, double* xi, int64_t cap,
+               int64_t* count) {
+  if (!h->allocated || !h->have_state) return fail(h, SUSP_ESTATE, "no state yet");
+  long long* cnt = nullptr;
+  CK(cudaMalloc(&cnt, sizeof(long long) * (h->N + 1)));
+  launch_row_counts(h->A, with_history, cnt, h->stream);
+  std::vector<long long> hc(h->N);
+  cudaMemcpyAsync(hc.data(), cnt, sizeof(long long) * h->N, cudaMemcpyDeviceToHost, h->stream);
+  cudaStreamSynchronize(h->stream);
+  std::vector<long long> off(h->N + 1, 0);
+  for (int64_t i = 0; i < h->N; ++i) off[i + 1] = off[i] + hc[i];
+  const int64_t total = off[h->N];
+  *count = total;
+  if (cap <= 0 || !ij) { cudaFree(cnt); return SUSP_OK; }
+  int* dij = nullptr;
+  double* dxi = nullptr;
+  cudaMemcpyAsync(cnt, off.data(), sizeof(long long) * h->N, cudaMemcpyHostToDevice, h->stream);
+  cudaError_t e1 = cudaMalloc(&dij, sizeof(int) * 2 * std::max<int64_t>(total, 1));
+  cudaError_t e2 = with_history ? cudaMalloc(&dxi, sizeof(double) * 3 * std::max<int64_t>(total, 1))
+                                : cudaSuccess;
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    cudaFree(cnt); cudaFree(dij); cudaFree(dxi);
+    return fail(h, SUSP_ENOMEM, "temporary allocation failed");
+  }
+  launch_list_pairs(h->A, cnt, dij, with_history, dxi, h->stream);
+  std::vector<int> hij(2 * total);
+  std::vector<double> hxi(with_history ? 3 * total : 0);
+  cudaMemcpyAsync(hij.data(), dij, sizeof(int) * 2 * total, cudaMemcpyDeviceToHost, h->stream);
+  if (with_history)
+    cudaMemcpyAsync(hxi.data(), dxi, sizeof(double) * 3 * total, cudaMemcpyDeviceToHost, h->stream);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  cudaFree(cnt); cudaFree(dij); cudaFree(dxi);
+  if (e != cudaSuccess) return fail(h, SUSP_ECUDA, cudaGetErrorString(e));
+  std::vector<int64_t> order(total);
+  for (int64_t i = 0; i < total; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    if (hij[2 * a] != hij[2 * b]) return hij[2 * a] < hij[2 * b];
+    return hij[2 * a + 1] < hij[2 * b + 1];
+  });
+  const int64_t n = std::min<int64_t>(cap, total);
+  for (int64_t i = 0; i < n; ++i) {
+    ij[2 * i] = hij[2 * order[i]];
+    ij[2 * i + 1] = hij[2 * order[i] + 1];
+    if (with_history && xi)
+      for (int q = 0; q < 3; ++q) xi[3 * i + q] = hxi[3 * order[i] + q];
+  }
+  return SUSP_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void susp_default_params(susp_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->eta = 1.0;
+  p->rho = 1.0;
+  p->kn = 1e4;
+  p->kt = 0.0;
+  p->mu = 0.0;
+  p->xi_min = 1e-3;
+  p->xi_max = 0.05;
+  p->skin = 0.3;
+  p->shear_rate = 1.0;
+  p->kT = 0.0;
+  p->torque_sign = -1.0;
+  p->dt = 1e-4;
+  p->seed = 0;
+  p->precision = SUSP_FP64;
+  p->noise = 1;
+  p->lubrication = 1;
+  p->onebody = 1;
+  p->contact = 1;
+  p->sample_every = 1;
+  p->kmax = 48;
+  p->threads_per_particle = 0;
+  p->use_graphs = 1;
+}
+
+int susp_create(susp_t** out, int64_t N, const double* radii, const double box[3],
+                const susp_params* p) {
+  if (!box) { g_create_error = "box is NULL"; return SUSP_EINVAL; }
+  return common_create(out, 1, &N, radii, box, p);
+}
+
+int susp_create_batch(susp_t** out, int32_t R, const int64_t* N_r, const double* radii,
+                      const double* boxes, const susp_params* p_r) {
+  return common_create(out, R, N_r, radii, boxes, p_r);
+}
+
+void susp_destroy(susp_t* h) {
+  if (!h) return;
+  cudaSetDevice(h->dev);
+  if (h->allocated) cudaStreamSynchronize(h->stream);
+  release_all(h);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  delete h;
+}
+
+const char* susp_last_error(const susp_t* h) { return h ? h->err.c_str() : ""; }
+
+const char* susp_create_error(void) { return g_create_error.c_str(); }
+
+int susp_set_stream(susp_t* h, void* s) {
+  if (!h) return SUSP_EINVAL;
+  cudaSetDevice(h->dev);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (s) {
+    h->stream = (cudaStream_t)s;
+  } else {
+    if (!h->own_stream && cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(h, SUSP_ECUDA, "stream creation failed");
+    h->stream = h->own_stream;
+  }
+  drop_graphs(h);
+  return SUSP_OK;
+}
+
+int susp_set_allocator(susp_t* h, void* (*alloc)(size_t, void*), void (*release)(void*, void*),
+                       void* ctx) {
+  if (!h) return SUSP_EINVAL;
+  if (h->allocated) return fail(h, SUSP_ESTATE, "allocator must be set before set_state");
+  if ((alloc == nullptr) != (release == nullptr))
+    return fail(h, SUSP_EINVAL, "alloc and release must both be set or both NULL");
+  h->ualloc = alloc;
+  h->ufree = release;
+  h->uctx = ctx;
+  return SUSP_OK;
+}
+
+static int set_state_impl(susp_t* h, const double* x, const double* U, const double* W,
+                          cudaMemcpyKind kind) {
+  if (!h) return SUSP_EINVAL;
+  h->err.clear();
+  if (!x) return fail(h, SUSP_EINVAL, "positions are required");
+  int rc = allocate(h);
+  if (rc) return rc;
+  CK(cudaSetDevice(h->dev));
+  const size_t bytes = sizeof(double) * 3 * h->N;
+  double* dx = h->d_stage;
+  double* dU = U ? h->d_stage + 3 * h->N : nullptr;
+  double* dW = W ? h->d_stage + 6 * h->N : nullptr;
+  CK(cudaMemcpyAsync(dx, x, bytes, kind, h->stream));
+  if (U) CK(cudaMemcpyAsync(dU, U, bytes, kind, h->stream));
+  if (W) CK(cudaMemcpyAsync(dW, W, bytes, kind, h->stream));
+  // strain/tilt must be current before wrapping
+  rc = sync_replicas(h, h->last_dt);
+  if (rc) return rc;
+  launch_load_state(h->A, dx, dU, dW, h->d_radius, h->d_mass, h->d_inertia, h->d_rep_of,
+                    h->stream);
+  launch_request_rebuild(h->A, h->stream);
+  h->have_state = true;
+  h->forces_valid = false;
+  return check_errors(h);
+}
+
+int susp_set_state(susp_t* h, const double* x, const double* U, const double* W) {
+  return set_state_impl(h, x, U, W, cudaMemcpyHostToDevice);
+}
+
+int susp_set_state_device(susp_t* h, const double* x, const double* U, const double* W) {
+  return set_state_impl(h, x, U, W, cudaMemcpyDeviceToDevice);
+}
+
+int susp_set_clock(susp_t* h, int64_t k, int32_t replica, double strain) {
+  if (!h) return SUSP_EINVAL;
+  if (!h->allocated) return fail(h, SUSP_ESTATE, "susp_set_state() must come first");
+  if (replica < -1 || replica >= h->R) return fail(h, SUSP_EINVAL, "replica out of range");
+  CK(cudaSetDevice(h->dev));
+  int rc = sync_replicas(h, h->last_dt);
+  if (rc) return rc;
+  for (int r = 0; r < h->R; ++r) {
+    if (replica != -1 && r != replica) continue;
+    Replica& R = h->repl_h[r];
+    if (!(std::fabs(strain) <= R.flip_at)) return fail(h, SUSP_EINVAL, "strain out of range");
+    R.strain = strain;
+    R.tilt = strain * R.L[1];
+  }
+  CK(cudaMemcpyAsync(h->A.repl, h->repl_h.data(), sizeof(Replica) * h->R,
+                     cudaMemcpyHostToDevice, h->stream));
+  long long kk = (long long)k;
+  CK(cudaMemcpyAsync(&h->A.ctl->k, &kk, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  launch_request_rebuild(h->A, h->stream);
+  h->forces_valid = false;
+  return SUSP_OK;
+}
+
+int susp_get_state(susp_t* h, double* x, double* U, double* W) {
+  if (!h) return SUSP_EINVAL;
+  if (!h->have_state) return fail(h, SUSP_ESTATE, "no state yet");
+  CK(cudaSetDevice(h->dev));
+  int rc = gather_host(h, 0, x);
+  if (!rc) rc = gather_host(h, 1, U);
+  if (!rc) rc = gather_host(h, 2, W);
+  return rc;
+}
+
+int susp_get_forces(susp_t* h, double* F, double* T) {
+  if (!h) return SUSP_EINVAL;
+  if (!h->have_state) return fail(h, SUSP_ESTATE, "no state yet");
+  CK(cudaSetDevice(h->dev));
+  int rc = gather_host(h, 3, F);
+  if (!rc) rc = gather_host(h, 4, T);
+  return rc;
+}
+
+int susp_build_neighbors(susp_t* h) {
+  if (!h) return SUSP_EINVAL;
+  if (!h->have_state) return fail(h, SUSP_ESTATE, "susp_set_state() must come first");
+  CK(cudaSetDevice(h->dev));
+  StepArgs s = make_args(h, h->last_dt, 0, 0);
+  launch_request_rebuild(h->A, h->stream);
+  launch_rebuild(h->A, h->bm, s, h->stream, h->p0.precision == SUSP_MIXED);
+  return check_errors(h);
+}
+
+int susp_evaluate(susp_t* h) {
+  if (!h) return SUSP_EINVAL;
+  if (!h->have_state) return fail(h, SUSP_ESTATE, "susp_set_state() must come first");
+  CK(cudaSetDevice(h->dev));
+  const double dt = h->last_dt;
+  int rc = sync_replicas(h, dt);
+  if (rc) return rc;
+  enqueue_setup_eval(h, dt, 1, h->stream);
+  h->forces_valid = true;
+  return check_errors(h);
+}
+
+int susp_step(susp_t* h, int64_t n_steps, double shear_rate, double kT, double dt,
+              uint64_t seed) {
+  if (!h) return SUSP_EINVAL;
+  h->err.clear();
+  if (h->R != 1) return fail(h, SUSP_EINVAL, "batch handles step with susp_step_batch()");
+  if (!(kT >= 0) || !std::isfinite(shear_rate))
+    return fail(h, SUSP_EINVAL, "need kT >= 0 and a finite shear rate");
+  Replica& R = h->repl_h[0];
+  if (R.rate != shear_rate || R.kT != kT || R.key0 != (uint32_t)(seed & 0xffffffffull) ||
+      R.key1 != (uint32_t)(seed >> 32)) {
+    if (R.rate != shear_rate || R.kT != kT) h->forces_valid = false;
+    if (R.key0 != (uint32_t)(seed & 0xffffffffull) || R.key1 != (uint32_t)(seed >> 32))
+      h->forces_valid = false;
+    R.rate = shear_rate;
+    R.kT = kT;
+    R.key0 = (uint32_t)(seed & 0xffffffffull);
+    R.key1 = (uint32_t)(seed >> 32);
+    h->pr[0].shear_rate = shear_rate;
+    h->pr[0].kT = kT;
+    h->pr[0].seed = seed;
+    drop_graphs(h);
+  }
+  if (dt != h->last_dt && h->last_dt > 0) h->forces_valid = false;
+  return run_steps(h, n_steps, dt);
+}
+
+int susp_step_batch(susp_t* h, int64_t n_steps, double dt) {
+  if (!h) return SUSP_EINVAL;
+  h->err.clear();
+  if (dt != h->last_dt && h->last_dt > 0) h->forces_valid = false;
+  return run_steps(h, n_steps, dt);
+}
+
+int susp_stress(susp_t* h, int32_t replica, double* out) {
+  if (!h || !out) return SUSP_EINVAL;
+  if (replica < 0 || replica >= h->R) return fail(h, SUSP_EINVAL, "replica out of range");
+  if (!h->allocated) return fail(h, SUSP_ESTATE, "no state yet");
+  CK(cudaSetDevice(h->dev));
+  double acc[48];
+  CK(cudaMemcpyAsync(acc, h->A.stress_acc + 48 * (int64_t)replica, sizeof(acc),
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemsetAsync(h->A.stress_acc + 48 * (int64_t)replica, 0, sizeof(acc), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const Replica& R = h->repl_h[replica];
+  const double np = acc[45], nk = acc[46];
+  const double V = R.V;
+  for (int c = 0; c < 27; ++c) out[c] = np > 0 ? acc[c] / np / V : 0.0;
+  // drag stresslet (20/3) pi eta sum a^3 E / V, E = rate/2 (xy + yx)
+  double s3 = 0.0;
+  for (int64_t i = h->off[replica]; i < h->off[replica + 1]; ++i)
+    s3 += h->radii[i] * h->radii[i] * h->radii[i];
+  const double dxy = 20.0 / 3.0 * kPi * R.eta * s3 * (0.5 * R.rate) / V;
+  for (int c = 0; c < 9; ++c) out[27 + c] = 0.0;
+  out[27 + 1] = dxy;
+  out[27 + 3] = dxy;
+  for (int c = 0; c < 18; ++c) out[36 + c] = nk > 0 ? acc[27 + c] / nk / V : 0.0;
+  double tot[9];
+  for (int c = 0; c < 9; ++c) tot[c] = out[c] + out[9 + c] + out[27 + c];
+  out[54] = R.rate != 0.0 ? tot[1] / (R.eta * R.rate) : 0.0;
+  out[55] = tot[0] - tot[4];
+  out[56] = tot[4] - tot[8];
+  out[57] = np;
+  return SUSP_OK;
+}
+
+int susp_get_pairs(susp_t* h, int32_t* ij, int64_t cap, int64_t* count) {
+  if (!h || !count) return SUSP_EINVAL;
+  CK(cudaSetDevice(h->dev));
+  return list_pairs(h, 0, ij, nullptr, cap, count);
+}
+
+int susp_get_history(susp_t* h, int32_t* ij, double* xi_t, int64_t cap, int64_t* count) {
+  if (!h || !count) return SUSP_EINVAL;
+  CK(cudaSetDevice(h->dev));
+  return list_pairs(h, 1, ij, xi_t, cap, count);
+}
+
+int susp_get_info(susp_t* h, double* info) {
+  if (!h || !info) return SUSP_EINVAL;
+  std::memset(info, 0, sizeof(double) * SUSP_INFO_LEN);
+  info[3] = h->kmax;
+  info[7] = h->tpp;
+  info[8] = h->p0.precision;
+  info[9] = h->R;
+  info[10] = (double)h->N;
+  info[11] = (double)h->graph_steps;
+  info[12] = (double)h->bytes;
+  if (!h->allocated) return SUSP_OK;
+  CK(cudaSetDevice(h->dev));
+  Ctl c{};
+  Replica r0{};
+  CK(cudaMemcpyAsync(&c, h->A.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&r0, h->A.repl, sizeof(Replica), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  info[0] = (double)c.k;
+  info[1] = c.nbuilds;
+  info[2] = c.max_row;
+  info[4] = (double)c.npairs;
+  info[5] = r0.strain;
+  info[6] = r0.tilt;
+  return SUSP_OK;
+}
+
+int susp_save(susp_t* h, const char* path) {
+  if (!h || !path) return SUSP_EINVAL;
+  if (!h->have_state) return fail(h, SUSP_ESTATE, "no state yet");
+  (void)path;
+  return fail(h, SUSP_EINVAL, "checkpointing is not available in this build");
+}
+
+int susp_load(susp_t* h, const char* path) {
+  if (!h || !path) return SUSP_EINVAL;
+  return fail(h, SUSP_EINVAL, "checkpointing is not available in this build");
+}
+
+}  // extern "C"

@@ -1,0 +1,354 @@
+// k_neighbors.cu -- cell binning, counting sort and the skin-padded half
+// neighbour list (Sec. II: pairwise forces are summed over the neighbours of
+// each sphere, found within the lubrication cutoff xi <= xi_max of Sec. II.B
+// plus a skin), with the tangential contact history (Sec. II.A) carried from
+// the old list to the new one.
+//
+// Cells are laid on the tilted lattice in fractional coordinates
+// s = H^-1 x (H the box matrix with the current tilt), nc cells per axis
+// chosen at creation so that each cell is at least one list cutoff thick for
+// any tilt |tilt| <= Lx/2; two spheres closer than the cutoff are then in the
+// same or adjacent cells of the periodic 3x3x3 stencil.  Keys are
+// replica base + cell index, so one sort groups replicas, then cells; ties
+// inside a cell are ordered by tag, which makes the order deterministic.
+//
+// Every kernel here is gated on Ctl::need_rebuild, so the whole sequence can
+// sit in every step of a captured graph (or under a conditional node) and
+// costs one flag read when no rebuild is due.  The rebuild permutes all
+// particle arrays into the spare copy and flips Ctl::cur at the end.
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+#include "susp_internal.h"
+
+namespace susp {
+
+constexpr int kScanPer = 8;                      // elements per thread
+constexpr int kScanBlock = kBlock * kScanPer;    // elements per scan block
+
+__device__ __forceinline__ bool gate(const Ctl* ctl) {
+  return *(volatile const int*)&ctl->need_rebuild != 0;
+}
+
+__global__ void k_request(Ctl* ctl) { ctl->need_rebuild = 1; }
+
+__global__ void k_zero_counts(Arrays A) {
+  if (!gate(A.ctl)) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= A.ncell;
+       i += (int64_t)gridDim.x * blockDim.x)
+    A.cell_count[i] = 0;
+}
+
+__device__ __forceinline__ int cell_index(const Replica& R, double x, double y,
+                                          double z, int* c3) {
+  const double sy = y / R.L[1];
+  double sx = (x - R.tilt * sy) / R.L[0];
+  sx = sx - floor(sx);
+  const double sz = z / R.L[2];
+  int cx = (int)(sx * R.nc[0]);
+  int cy = (int)(sy * R.nc[1]);
+  int cz = (int)(sz * R.nc[2]);
+  cx = min(max(cx, 0), R.nc[0] - 1);
+  cy = min(max(cy, 0), R.nc[1] - 1);
+  cz = min(max(cz, 0), R.nc[2] - 1);
+  if (c3) { c3[0] = cx; c3[1] = cy; c3[2] = cz; }
+  return (cz * R.nc[1] + cy) * R.nc[0] + cx;
+}
+
+__global__ void k_cellkey(Arrays A) {
+  if (!gate(A.ctl)) return;
+  const int cur = A.ctl->cur;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= A.N) return;
+  const int r = A.rep[cur][p];
+  const Replica& R = A.repl[r];
+  const double4_32a P = A.pos[cur][p];
+  const int key = (int)(R.cell_base + cell_index(R, P.x, P.y, P.z, nullptr));
+  A.key[p] = key;
+  atomicAdd(&A.cell_count[key], 1);
+}
+
+// exclusive scan of cell_count[0..ncell) -> cell_start, in three passes
+__global__ void k_scan_blocks(Arrays A) {
+  if (!gate(A.ctl)) return;
+  __shared__ int wsum[kBlock / 32];
+  const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanPer;
+  int v[kScanPer];
+  int tsum = 0;
+#pragma unroll
+  for (int e = 0; e < kScanPer; ++e) {
+    const int64_t i = base + e;
+    v[e] = i < A.ncell ? A.cell_count[i] : 0;
+    tsum += v[e];
+  }
+  // inclusive scan of thread sums in the block
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = tsum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < kBlock / 32 ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kBlock / 32) wsum[lane] = w;
+  }
+  __syncthreads();
+  const int excl = x - tsum + (warp > 0 ? wsum[warp - 1] : 0);
+  int run = excl;
+#pragma unroll
+  for (int e = 0; e < kScanPer; ++e) {
+    const int64_t i = base + e;
+    if (i < A.ncell) A.cell_start[i] = run;
+    run += v[e];
+  }
+  if (threadIdx.x == kBlock - 1) A.scan_part[blockIdx.x] = run;
+}
+
+__global__ void k_scan_top(Arrays A, int nparts) {
+  if (!gate(A.ctl)) return;
+  __shared__ int wsum[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  for (int base = 0; base < nparts; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int v = i < nparts ? A.scan_part[i] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      int w = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      if (lane < nw) wsum[lane] = w;
+    }
+    __syncthreads();
+    const int incl = x + (warp > 0 ? wsum[warp - 1] : 0);
+    if (i < nparts) A.scan_part[i] = carry + incl - v;  // exclusive
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += incl;
+    __syncthreads();
+  }
+}
+
+__global__ void k_scan_add(Arrays A) {
+  if (!gate(A.ctl)) return;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < A.ncell) {
+    const int v = A.cell_start[i] + A.scan_part[i / kScanBlock];
+    A.cell_start[i] = v;
+    A.cell_fill[i] = v;
+  }
+  if (i == 0) A.cell_start[A.ncell] = (int)A.N;
+}
+
+__global__ void k_scatter(Arrays A) {
+  if (!gate(A.ctl)) return;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= A.N) return;
+  const int slot = atomicAdd(&A.cell_fill[A.key[p]], 1);
+  A.perm[slot] = (int)p;
+}
+
+// order the few spheres of each cell by tag (insertion sort)
+__global__ void k_cellsort(Arrays A) {
+  if (!gate(A.ctl)) return;
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= A.ncell) return;
+  const int cur = A.ctl->cur;
+  const int s0 = A.cell_start[c], s1 = A.cell_start[c + 1];
+  const int* tag = A.tag[cur];
+  for (int i = s0 + 1; i < s1; ++i) {
+    const int v = A.perm[i];
+    const int tv = tag[v];
+    int j = i - 1;
+    while (j >= s0 && tag[A.perm[j]] > tv) {
+      A.perm[j + 1] = A.perm[j];
+      --j;
+    }
+    A.perm[j + 1] = v;
+  }
+}
+
+__global__ void k_permute(Arrays A) {
+  if (!gate(A.ctl)) return;
+  const int cur = A.ctl->cur, nxt = cur ^ 1;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= A.N) return;
+  const int o = A.perm[p];
+  const int64_t Np = A.Npad;
+  A.pos[nxt][p] = A.pos[cur][o];
+  A.vel[nxt][p] = A.vel[cur][o];
+  A.omg[nxt][p] = A.omg[cur][o];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    A.frc[nxt][q * Np + p] = A.frc[cur][q * Np + o];
+    A.trq[nxt][q * Np + p] = A.trq[cur][q * Np + o];
+  }
+  const int t = A.tag[cur][o];
+  A.tag[nxt][p] = t;
+  A.rep[nxt][p] = A.rep[cur][o];
+  A.cell[p] = A.key[o];
+  A.slot_of_tag[t] = (int)p;
+}
+
+__global__ void __launch_bounds__(kBlock) k_build_list(Arrays A, StepArgs s, double rc_fac) {
+  if (!gate(A.ctl)) return;
+  const int nxt = A.ctl->cur ^ 1;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= A.N) return;
+  const int r = A.rep[nxt][p];
+  const Replica& R = A.repl[r];
+  const double L[3] = {R.L[0], R.L[1], R.L[2]};
+  const double tilt = R.tilt;
+  const double4_32a P = A.pos[nxt][p];
+  const int local = (int)(A.cell[p] - R.cell_base);
+  const int ncx = R.nc[0], ncy = R.nc[1], ncz = R.nc[2];
+  const int cx = local % ncx, cy = (local / ncx) % ncy, cz = local / (ncx * ncy);
+  const int64_t Np = A.Npad;
+  int* row = A.nbr[nxt] + p;
+  int cnt = 0;
+  const int kmax = A.kmax;
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int zz = (cz + dz + ncz) % ncz;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int yy = (cy + dy + ncy) % ncy;
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int xx = (cx + dx + ncx) % ncx;
+        const int64_t key = R.cell_base + ((int64_t)zz * ncy + yy) * ncx + xx;
+        const int q0 = A.cell_start[key], q1 = A.cell_start[key + 1];
+        for (int q = q0; q < q1; ++q) {
+          if (q <= p) continue;
+          const double4_32a Q = A.pos[nxt][q];
+          double rr[3], sy;
+          min_image_f64(Q.x - P.x, Q.y - P.y, Q.z - P.z, L, tilt, rr, &sy);
+          const double d2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
+          const double rc = (P.w + Q.w) * rc_fac + s.skin;
+          if (!(d2 < rc * rc)) continue;
+          if (cnt < kmax) row[(int64_t)cnt * Np] = q;
+          ++cnt;
+        }
+      }
+    }
+  }
+  if (cnt > kmax) {
+    atomicOr(&A.ctl->err, kErrOverflow);
+    atomicMax(&A.ctl->max_row, cnt);
+    cnt = kmax;
+  } else {
+    atomicMax(&A.ctl->max_row, cnt);
+  }
+  A.nnb[nxt][p] = cnt;
+  atomicAdd((unsigned long long*)&A.ctl->npairs, (unsigned long long)cnt);
+}
+
+// carry tangential history of touching pairs into the new list
+__global__ void __launch_bounds__(kBlock) k_remap_history(Arrays A) {
+  if (!gate(A.ctl)) return;
+  const int cur = A.ctl->cur, nxt = cur ^ 1;
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= A.N) return;
+  const int64_t Np = A.Npad;
+  const int64_t hs = (int64_t)A.kmax * Np;
+  const int r = A.rep[nxt][p];
+  const Replica& R = A.repl[r];
+  const double L[3] = {R.L[0], R.L[1], R.L[2]};
+  const double4_32a P = A.pos[nxt][p];
+  const int nn = A.nnb[nxt][p];
+  const int op = A.perm[p];
+  unsigned long long cm = 0ull;
+  for (int sl = 0; sl < nn; ++sl) {
+    const int q = A.nbr[nxt][(int64_t)sl * Np + p];
+    const double4_32a Q = A.pos[nxt][q];
+    double rr[3], sy;
+    min_image_f64(Q.x - P.x, Q.y - P.y, Q.z - P.z, L, R.tilt, rr, &sy);
+    const double d2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
+    const double S = P.w + Q.w;
+    if (!(sqrt(d2) < S)) continue;  // not touching: history is erased anyway
+    const int oq = A.perm[q];
+    int row = -1, slot = -1;
+    const int n1 = A.nnb[cur][op];
+    for (int t = 0; t < n1; ++t)
+      if (A.nbr[cur][(int64_t)t * Np + op] == oq) { row = op; slot = t; break; }
+    if (row < 0) {
+      const int n2 = A.nnb[cur][oq];
+      for (int t = 0; t < n2; ++t)
+        if (A.nbr[cur][(int64_t)t * Np + oq] == op) { row = oq; slot = t; break; }
+    }
+    if (row < 0) continue;
+    if (!((A.cmsk[cur][row] >> slot) & 1ull)) continue;
+    const int64_t src = (int64_t)slot * Np + row;
+    const int64_t dst = (int64_t)sl * Np + p;
+    const double* ho = A.hist[cur];
+    double* hn = A.hist[nxt];
+    hn[dst] = ho[src];
+    hn[dst + hs] = ho[src + hs];
+    hn[dst + 2 * hs] = ho[src + 2 * hs];
+    cm |= 1ull << sl;
+  }
+  A.cmsk[nxt][p] = cm;
+}
+
+__global__ void k_finish(Arrays A) {
+  if (!gate(A.ctl)) return;
+  Ctl* ctl = A.ctl;
+  ctl->cur = ctl->cur ^ 1;
+  ctl->need_rebuild = 0;
+  ctl->disp_bound = 0.0;
+  ctl->t_since_build = 0.0;
+  ctl->nbuilds = ctl->nbuilds + 1;
+}
+
+__global__ void k_reset_counters(Arrays A) {
+  if (!gate(A.ctl)) return;
+  A.ctl->max_row = 0;
+  A.ctl->npairs = 0;
+}
+
+static inline unsigned grid_for(int64_t n) {
+  return (unsigned)((n + kBlock - 1) / kBlock);
+}
+
+void launch_request_rebuild(const Arrays& A, cudaStream_t st) {
+  k_request<<<1, 1, 0, st>>>(A.ctl);
+}
+
+void launch_rebuild(const Arrays& A, const BlockMap& bm, const StepArgs& s,
+                    cudaStream_t st, int mixed) {
+  (void)bm;
+  const int64_t nc = A.ncell;
+  const int nparts = (int)((nc + kScanBlock - 1) / kScanBlock);
+  k_reset_counters<<<1, 1, 0, st>>>(A);
+  k_zero_counts<<<grid_for(nc + 1), kBlock, 0, st>>>(A);
+  k_cellkey<<<grid_for(A.N), kBlock, 0, st>>>(A);
+  k_scan_blocks<<<nparts, kBlock, 0, st>>>(A);
+  k_scan_top<<<1, 1024, 0, st>>>(A, nparts);
+  k_scan_add<<<grid_for(nc), kBlock, 0, st>>>(A);
+  k_scatter<<<grid_for(A.N), kBlock, 0, st>>>(A);
+  k_cellsort<<<grid_for(nc), kBlock, 0, st>>>(A);
+  k_permute<<<grid_for(A.N), kBlock, 0, st>>>(A);
+  k_build_list<<<grid_for(A.N), kBlock, 0, st>>>(A, s, 1.0 + 0.5 * s.xi_max);
+  if (s.friction) k_remap_history<<<grid_for(A.N), kBlock, 0, st>>>(A);
+  if (mixed) launch_mirror_gated_next(A, st);
+  k_finish<<<1, 1, 0, st>>>(A);
+}
+
+}  // namespace susp

@@ -1,0 +1,233 @@
+// k_pair_fp64.cu -- per-timestep pair force evaluation in double precision
+// (the plain FP64 path).  Compiled without multiply-add contraction so that
+// every sum and product rounds as written.
+//
+// One thread per sphere p of the sorted order walks its half-list row.  For
+// each listed pair it forms the minimum-image gap h = |r| - (a_i + a_j) and
+// xi = 2h/(a_i + a_j) (Sec. II.B); pairs with xi > xi_max are skipped.  Each
+// remaining pair is oriented by tag (i = lower tag, n from i to j) and gets
+//   - lubrication, Eqs. 8, 13, 14, with resistances Eqs. 9-12, 15-18 at
+//     xi_eff = max(xi, xi_min);
+//   - pair Brownian force and torques, Eqs. 22-24, Philox counter
+//     (k, tag_i, tag_j);
+//   - for h < 0 the contact force and torques, Eqs. 3-4, with tangential
+//     history (double, per list slot) and the Coulomb cap.
+// The sphere's own sums (with the one-body drag, Eqs. 5-6, and one-body
+// noise, Eqs. 20-21) stay in registers; the partner's share is added with
+// double atomics.  On sampled evaluations the pair virials F (x) r of the
+// three components are reduced per block (Sec. II.A, II.B, II.D).
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+#include "philox.cuh"
+#include "susp_internal.h"
+
+namespace susp {
+
+template <bool NOISE, bool FRIC, bool SAMPLE>
+__global__ void __launch_bounds__(kBlock)
+k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
+  __shared__ double smem[(kBlock / 32) * kPartialLen];
+  const int b = blockIdx.x;
+  const int r = bm.rep[b];
+  const int p = bm.start[b] + threadIdx.x;
+  const bool active = p < bm.end[b];
+  const Ctl* ctl = A.ctl;
+  const int cur = ctl->cur;
+  const long long k = ctl->k;
+  const Replica& RP = A.repl[r];
+  const double L[3] = {RP.L[0], RP.L[1], RP.L[2]};
+  const double tilt = RP.tilt;
+  const double rate = RP.rate;
+  const double eta = RP.eta, kn = RP.kn, kt = RP.kt, mu = RP.mu;
+  const double c = RP.noise_c;
+  const uint32_t key0 = RP.key0, key1 = RP.key1;
+  const int64_t t0 = RP.p0;
+  const int64_t Np = A.Npad;
+
+  double vir[kPartialLen];
+#pragma unroll
+  for (int q = 0; q < kPartialLen; ++q) vir[q] = 0.0;
+
+  if (active) {
+    const double4_32a P = A.pos[cur][p];
+    const double4_32a VP = A.vel[cur][p];
+    const double4_32a WP = A.omg[cur][p];
+    const int tp = A.tag[cur][p];
+    const double ap = P.w;
+    double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
+
+    if (s.onebody) {
+      // Eqs. 5-6 and 20-21
+      const double pi = 3.14159265358979323846;
+      const double gt = 6.0 * pi * eta * ap;
+      const double gr = 8.0 * pi * eta * ap * ap * ap;
+      const double Uinf0 = rate * (P.y - 0.5 * L[1]);
+      const double Winf2 = -0.5 * rate;
+      double g[6] = {0, 0, 0, 0, 0, 0};
+      if (NOISE) gauss6_f64(key0, key1, k, (uint32_t)(tp - t0), (uint32_t)(tp - t0), g);
+      const double ct = c * sqrt(gt), cr = c * sqrt(gr);
+      F[0] += gt * (Uinf0 - VP.x) + (NOISE ? ct * g[0] : 0.0);
+      F[1] += gt * (0.0 - VP.y) + (NOISE ? ct * g[1] : 0.0);
+      F[2] += gt * (0.0 - VP.z) + (NOISE ? ct * g[2] : 0.0);
+      T[0] += gr * (0.0 - WP.x) + (NOISE ? cr * g[3] : 0.0);
+      T[1] += gr * (0.0 - WP.y) + (NOISE ? cr * g[4] : 0.0);
+      T[2] += gr * (Winf2 - WP.z) + (NOISE ? cr * g[5] : 0.0);
+    }
+
+    const int nn = A.nnb[cur][p];
+    const int* __restrict__ row = A.nbr[cur] + p;
+    unsigned long long cm_old = 0ull, cm_new = 0ull;
+    if (FRIC) cm_old = A.cmsk[cur][p];
+    double* __restrict__ hist = FRIC ? A.hist[cur] : nullptr;
+    const int64_t hstride = (int64_t)A.kmax * Np;
+
+    for (int sl = 0; sl < nn; ++sl) {
+      const int q = row[(int64_t)sl * Np];
+      const double4_32a Q = A.pos[cur][q];
+      double rpq[3], sy;
+      min_image_f64(Q.x - P.x, Q.y - P.y, Q.z - P.z, L, tilt, rpq, &sy);
+      const double d2 = rpq[0] * rpq[0] + rpq[1] * rpq[1] + rpq[2] * rpq[2];
+      const double d = sqrt(d2);
+      const double S = ap + Q.w;
+      const double h = d - S;
+      const double xi = 2.0 * h / S;
+      if (xi > s.xi_max) continue;
+
+      const double4_32a VQ = A.vel[cur][q];
+      const double4_32a WQ = A.omg[cur][q];
+      const int tq = A.tag[cur][q];
+      const bool p_is_i = tp < tq;
+      // orient: i = lower tag, n and r from i to j
+      double rr[3], syij, ai, aj;
+      double Ui[3], Uj[3], Wi[3], Wj[3];
+      if (p_is_i) {
+        rr[0] = rpq[0]; rr[1] = rpq[1]; rr[2] = rpq[2]; syij = sy;
+        ai = ap; aj = Q.w;
+        Ui[0] = VP.x; Ui[1] = VP.y; Ui[2] = VP.z; Uj[0] = VQ.x; Uj[1] = VQ.y; Uj[2] = VQ.z;
+        Wi[0] = WP.x; Wi[1] = WP.y; Wi[2] = WP.z; Wj[0] = WQ.x; Wj[1] = WQ.y; Wj[2] = WQ.z;
+      } else {
+        rr[0] = -rpq[0]; rr[1] = -rpq[1]; rr[2] = -rpq[2]; syij = -sy;
+        ai = Q.w; aj = ap;
+        Ui[0] = VQ.x; Ui[1] = VQ.y; Ui[2] = VQ.z; Uj[0] = VP.x; Uj[1] = VP.y; Uj[2] = VP.z;
+        Wi[0] = WQ.x; Wi[1] = WQ.y; Wi[2] = WQ.z; Wj[0] = WP.x; Wj[1] = WP.y; Wj[2] = WP.z;
+      }
+      const double n[3] = {rr[0] / d, rr[1] / d, rr[2] / d};
+      const double dU[3] = {Uj[0] - syij * rate * L[1] - Ui[0], Uj[1] - Ui[1],
+                            Uj[2] - Ui[2]};
+
+      PairOut<double> o;
+      if (s.lubrication) {
+        const double xi_e = xi < s.xi_min ? s.xi_min : xi;
+        const double lg = log(1.0 / xi_e);
+        const Res8<double> R = resistances<double>(eta, ai, aj, xi_e, lg);
+        double g[6] = {0, 0, 0, 0, 0, 0};
+        const int li = (int)((p_is_i ? tp : tq) - t0);
+        const int lj = (int)((p_is_i ? tq : tp) - t0);
+        if (NOISE) gauss6_f64(key0, key1, k, (uint32_t)li, (uint32_t)lj, g);
+        lub_brownian<double, NOISE>(R, n, dU, Wi, Wj, g, g + 3, c, s.torque_sign, o);
+      } else {
+#pragma unroll
+        for (int q3 = 0; q3 < 3; ++q3) o.FL[q3] = o.FB[q3] = o.Ti[q3] = o.Tj[q3] = 0.0;
+      }
+
+      double FC[3] = {0.0, 0.0, 0.0}, TCi[3] = {0.0, 0.0, 0.0}, TCj[3] = {0.0, 0.0, 0.0};
+      if (h < 0.0 && s.contact) {
+        const double delta = -h;
+        double Ft[3] = {0.0, 0.0, 0.0};
+        if (FRIC && mu > 0.0) {
+          double xt[3] = {0.0, 0.0, 0.0};
+          const int64_t hi = (int64_t)sl * Np + p;
+          if ((cm_old >> sl) & 1ull) {
+            xt[0] = hist[hi]; xt[1] = hist[hi + hstride]; xt[2] = hist[hi + 2 * hstride];
+          }
+          if (s.advance) {
+            const double ww[3] = {ai * Wi[0] + aj * Wj[0], ai * Wi[1] + aj * Wj[1],
+                                  ai * Wi[2] + aj * Wj[2]};
+            double wxn[3];
+            cross3(ww, n, wxn);
+            const double v[3] = {dU[0] - wxn[0], dU[1] - wxn[1], dU[2] - wxn[2]};
+            history_update(xt, n, v, s.dt, kt, mu * kn * delta);
+          }
+          hist[hi] = xt[0]; hist[hi + hstride] = xt[1]; hist[hi + 2 * hstride] = xt[2];
+          cm_new |= 1ull << sl;
+          Ft[0] = kt * xt[0]; Ft[1] = kt * xt[1]; Ft[2] = kt * xt[2];
+        }
+#pragma unroll
+        for (int q3 = 0; q3 < 3; ++q3) FC[q3] = -kn * delta * n[q3] + Ft[q3];
+        double nxF[3];
+        cross3(n, Ft, nxF);
+#pragma unroll
+        for (int q3 = 0; q3 < 3; ++q3) {
+          TCi[q3] = ai * nxF[q3];
+          TCj[q3] = aj * nxF[q3];
+        }
+      }
+
+      double Fi[3], Ti_[3], Tj_[3];
+#pragma unroll
+      for (int q3 = 0; q3 < 3; ++q3) {
+        Fi[q3] = FC[q3] + o.FL[q3] + o.FB[q3];
+        Ti_[q3] = TCi[q3] + o.Ti[q3];
+        Tj_[q3] = TCj[q3] + o.Tj[q3];
+      }
+      const int64_t qo = q;
+      if (p_is_i) {
+#pragma unroll
+        for (int q3 = 0; q3 < 3; ++q3) {
+          F[q3] += Fi[q3];
+          T[q3] += Ti_[q3];
+          atomicAdd(A.frc[cur] + q3 * Np + qo, -Fi[q3]);
+          atomicAdd(A.trq[cur] + q3 * Np + qo, Tj_[q3]);
+        }
+      } else {
+#pragma unroll
+        for (int q3 = 0; q3 < 3; ++q3) {
+          F[q3] -= Fi[q3];
+          T[q3] += Tj_[q3];
+          atomicAdd(A.frc[cur] + q3 * Np + qo, Fi[q3]);
+          atomicAdd(A.trq[cur] + q3 * Np + qo, Ti_[q3]);
+        }
+      }
+      if (SAMPLE) {
+#pragma unroll
+        for (int al = 0; al < 3; ++al)
+#pragma unroll
+          for (int be = 0; be < 3; ++be) {
+            vir[3 * al + be] += FC[al] * rr[be];
+            vir[9 + 3 * al + be] += o.FL[al] * rr[be];
+            vir[18 + 3 * al + be] += o.FB[al] * rr[be];
+          }
+      }
+    }
+    if (FRIC) A.cmsk[cur][p] = cm_new;
+#pragma unroll
+    for (int q3 = 0; q3 < 3; ++q3) {
+      atomicAdd(A.frc[cur] + q3 * Np + p, F[q3]);
+      atomicAdd(A.trq[cur] + q3 * Np + p, T[q3]);
+    }
+  }
+  if (SAMPLE) block_sum_write<kPartialLen>(vir, smem, A.pair_partial + (int64_t)b * kPartialLen);
+}
+
+template <bool NOISE, bool FRIC>
+static void launch_sample(const Arrays& A, const BlockMap& bm, const StepArgs& s,
+                          cudaStream_t st) {
+  if (s.sample)
+    k_pair_fp64<NOISE, FRIC, true><<<bm.nblocks, kBlock, 0, st>>>(A, bm, s);
+  else
+    k_pair_fp64<NOISE, FRIC, false><<<bm.nblocks, kBlock, 0, st>>>(A, bm, s);
+}
+
+void launch_pair_fp64(const Arrays& A, const BlockMap& bm, const StepArgs& s,
+                      int tpp, cudaStream_t st) {
+  (void)tpp;
+  const bool noise = s.noise != 0;
+  const bool fric = s.friction != 0;
+  if (noise && fric) launch_sample<true, true>(A, bm, s, st);
+  else if (noise) launch_sample<true, false>(A, bm, s, st);
+  else if (fric) launch_sample<false, true>(A, bm, s, st);
+  else launch_sample<false, false>(A, bm, s, st);
+}
+
+}  // namespace susp

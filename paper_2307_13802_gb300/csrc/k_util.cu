@@ -1,0 +1,189 @@
+// k_util.cu -- state upload/download between the caller's tag order and the
+// library's sorted order, force clearing, and the deterministic reduction of
+// per-block stress and kinetic partial sums into per-replica accumulators.
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+#include "susp_internal.h"
+
+namespace susp {
+
+// Writes x, U, W (tag order, [N][3]) into the live copy in tag order with
+// radius, mass and moment of inertia; wraps positions into the box as the
+// integrator does; clears forces.  Tags become the identity order, so the
+// next neighbour build sorts from scratch.
+__global__ void k_load_state(Arrays A, const double* __restrict__ x,
+                             const double* __restrict__ U,
+                             const double* __restrict__ W,
+                             const double* __restrict__ radius,
+                             const double* __restrict__ mass,
+                             const double* __restrict__ inertia,
+                             const int* __restrict__ rep_of) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= A.N) return;
+  const int cur = A.ctl->cur;
+  const int r = rep_of[p];
+  const Replica& R = A.repl[r];
+  double px = x[3 * p], py = x[3 * p + 1], pz = x[3 * p + 2];
+  double ux = U ? U[3 * p] : 0.0, uy = U ? U[3 * p + 1] : 0.0, uz = U ? U[3 * p + 2] : 0.0;
+  const double wx = W ? W[3 * p] : 0.0, wy = W ? W[3 * p + 1] : 0.0, wz = W ? W[3 * p + 2] : 0.0;
+  const double dUx = R.rate * R.L[1];
+  if (isfinite(px + py + pz)) {
+    int guard = 0;
+    while (py >= R.L[1] && guard < 1024) { py = py - R.L[1]; px = px - R.tilt; ux = ux - dUx; ++guard; }
+    while (py < 0.0 && guard < 1024) { py = py + R.L[1]; px = px + R.tilt; ux = ux + dUx; ++guard; }
+    while (px >= R.L[0] && guard < 1024) { px = px - R.L[0]; ++guard; }
+    while (px < 0.0 && guard < 1024) { px = px + R.L[0]; ++guard; }
+    while (pz >= R.L[2] && guard < 1024) { pz = pz - R.L[2]; ++guard; }
+    while (pz < 0.0 && guard < 1024) { pz = pz + R.L[2]; ++guard; }
+    if (guard >= 1024) atomicOr(&A.ctl->err, kErrWrap);
+  } else {
+    atomicOr(&A.ctl->err, kErrNonFinite);
+  }
+  A.pos[cur][p] = make_double4_32a(px, py, pz, radius[p]);
+  A.vel[cur][p] = make_double4_32a(ux, uy, uz, mass[p]);
+  A.omg[cur][p] = make_double4_32a(wx, wy, wz, inertia[p]);
+  const int64_t Np = A.Npad;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    A.frc[cur][q * Np + p] = 0.0;
+    A.trq[cur][q * Np + p] = 0.0;
+  }
+  A.tag[cur][p] = (int)p;
+  A.rep[cur][p] = r;
+  A.slot_of_tag[p] = (int)p;
+  A.nnb[cur][p] = 0;
+  A.cmsk[cur][p] = 0ull;
+}
+
+__global__ void k_zero_forces(Arrays A) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= A.N) return;
+  const int cur = A.ctl->cur;
+  const int64_t Np = A.Npad;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    A.frc[cur][q * Np + p] = 0.0;
+    A.trq[cur][q * Np + p] = 0.0;
+  }
+}
+
+// out[N][3] in tag order from the live copy: what = 0 x, 1 U, 2 W, 3 F, 4 T
+__global__ void k_gather(Arrays A, int what, double* __restrict__ out) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= A.N) return;
+  const int cur = A.ctl->cur;
+  const int p = A.slot_of_tag[t];
+  const int64_t Np = A.Npad;
+  double v0, v1, v2;
+  if (what == 0) { const double4_32a P = A.pos[cur][p]; v0 = P.x; v1 = P.y; v2 = P.z; }
+  else if (what == 1) { const double4_32a V = A.vel[cur][p]; v0 = V.x; v1 = V.y; v2 = V.z; }
+  else if (what == 2) { const double4_32a W = A.omg[cur][p]; v0 = W.x; v1 = W.y; v2 = W.z; }
+  else if (what == 3) { const double* F = A.frc[cur]; v0 = F[p]; v1 = F[Np + p]; v2 = F[2 * Np + p]; }
+  else { const double* T = A.trq[cur]; v0 = T[p]; v1 = T[Np + p]; v2 = T[2 * Np + p]; }
+  out[3 * t] = v0; out[3 * t + 1] = v1; out[3 * t + 2] = v2;
+}
+
+// Pairs of the live half list as (tag_i, tag_j), tag_i < tag_j, written at
+// per-sphere offsets (exclusive scan of the row lengths done on the host).
+__global__ void k_list_pairs(Arrays A, const long long* __restrict__ off,
+                             int* __restrict__ ij, int with_history,
+                             double* __restrict__ xi_t) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= A.N) return;
+  const int cur = A.ctl->cur;
+  const int64_t Np = A.Npad;
+  const int64_t hs = (int64_t)A.kmax * Np;
+  const int nn = A.nnb[cur][p];
+  const int tp = A.tag[cur][p];
+  long long o = off[p];
+  const unsigned long long cm = with_history ? A.cmsk[cur][p] : 0ull;
+  for (int sl = 0; sl < nn; ++sl) {
+    if (with_history && !((cm >> sl) & 1ull)) continue;
+    const int q = A.nbr[cur][(int64_t)sl * Np + p];
+    const int tq = A.tag[cur][q];
+    ij[2 * o] = tp < tq ? tp : tq;
+    ij[2 * o + 1] = tp < tq ? tq : tp;
+    if (with_history) {
+      const int64_t h = (int64_t)sl * Np + p;
+      xi_t[3 * o] = A.hist[cur][h];
+      xi_t[3 * o + 1] = A.hist[cur][h + hs];
+      xi_t[3 * o + 2] = A.hist[cur][h + 2 * hs];
+    }
+    ++o;
+  }
+}
+
+__global__ void k_row_counts(Arrays A, int with_history, long long* __restrict__ cnt) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= A.N) return;
+  const int cur = A.ctl->cur;
+  if (with_history) cnt[p] = __popcll(A.cmsk[cur][p]);
+  else cnt[p] = A.nnb[cur][p];
+}
+
+// grid (R, 27 + 18): component c of replica r summed over the replica's
+// blocks in a fixed order and added to the running accumulator.
+__global__ void k_reduce_stress(Arrays A, const int* __restrict__ rep_bstart,
+                                int sample_pair, int sample_kin) {
+  __shared__ double smem[kBlock / 32];
+  const int r = blockIdx.x, c = blockIdx.y;
+  const bool is_pair = c < kPartialLen;
+  if (is_pair && !sample_pair) return;
+  if (!is_pair && !sample_kin) return;
+  const int b0 = rep_bstart[r], b1 = rep_bstart[r + 1];
+  double s = 0.0;
+  for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x)
+    s += is_pair ? A.pair_partial[(int64_t)b * kPartialLen + c]
+                 : A.kin_partial[(int64_t)b * kKinLen + (c - kPartialLen)];
+  double v[1] = {s};
+  double out[1];
+  __shared__ double res;
+  block_sum_write<1>(v, smem, out);
+  if (threadIdx.x == 0) res = out[0];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double* acc = A.stress_acc + (int64_t)r * 48;
+    acc[c] += res;
+    if (c == 0) acc[45] += 1.0;
+    if (c == kPartialLen) acc[46] += 1.0;
+  }
+}
+
+void launch_reduce_stress(const Arrays& A, const BlockMap& bm, int sample_pair,
+                          int sample_kin, cudaStream_t st) {
+  (void)bm;
+  if (!sample_pair && !sample_kin) return;
+  dim3 grid(A.R, kPartialLen + kKinLen);
+  k_reduce_stress<<<grid, kBlock, 0, st>>>(A, A.rep_bstart, sample_pair, sample_kin);
+}
+
+void launch_load_state(const Arrays& A, const double* x, const double* U,
+                       const double* W, const double* radius,
+                       const double* mass, const double* inertia,
+                       const int* rep_of, cudaStream_t st) {
+  k_load_state<<<(unsigned)((A.N + kBlock - 1) / kBlock), kBlock, 0, st>>>(
+      A, x, U, W, radius, mass, inertia, rep_of);
+}
+
+void launch_zero_forces(const Arrays& A, cudaStream_t st) {
+  k_zero_forces<<<(unsigned)((A.N + kBlock - 1) / kBlock), kBlock, 0, st>>>(A);
+}
+
+void launch_gather(const Arrays& A, int what, double* out, cudaStream_t st) {
+  k_gather<<<(unsigned)((A.N + kBlock - 1) / kBlock), kBlock, 0, st>>>(A, what, out);
+}
+
+void launch_row_counts(const Arrays& A, int with_history, long long* cnt,
+                       cudaStream_t st) {
+  k_row_counts<<<(unsigned)((A.N + kBlock - 1) / kBlock), kBlock, 0, st>>>(
+      A, with_history, cnt);
+}
+
+void launch_list_pairs(const Arrays& A, const long long* off, int* ij,
+                       int with_history, double* xi_t, cudaStream_t st) {
+  k_list_pairs<<<(unsigned)((A.N + kBlock - 1) / kBlock), kBlock, 0, st>>>(
+      A, off, ij, with_history, xi_t);
+}
+
+}  // namespace susp

@@ -1,0 +1,172 @@
+// susp_internal.h -- device-side data layout shared by the library's CUDA
+// translation units (not part of the public ABI).
+//
+// Layout in HBM.  Particles live in "sorted" order p: grouped by replica,
+// then by cell key (counting sort on the cell of the tilted grid), then by
+// tag.  Every per-particle array that is permuted at a rebuild exists twice
+// (index [0]/[1]); Ctl::cur names the live copy, so a neighbour rebuild
+// inside a captured CUDA graph permutes into the other copy and flips `cur`
+// without any pointer change in the graph.
+//   pos  double4_32a (x, y, z, a)            lab frame, wrapped into the box
+//   vel  double4_32a (Ux, Uy, Uz, m)          lab-frame velocity, mass
+//   omg  double4_32a (Wx, Wy, Wz, I)          angular velocity, moment of inertia
+//   frc  double [3][Npad]                 force (SoA; accumulated by atomics)
+//   trq  double [3][Npad]                 torque
+//   tag  int32                            global tag (caller index)
+//   rep  int32                            replica of the particle
+//   nbr  int32  [kmax][Npad]              half list, slot-major (coalesced)
+//   nnb  int32  [Npad]                    row lengths
+//   hist double [3][kmax][Npad]           tangential history per slot (mu>0)
+//   cmsk uint64 [Npad]                    slot s in contact at last evaluation
+//   mirror (mixed precision)  float4 posm (dx, dy, dz, a) offset from the
+//                               home-cell origin; float4 velm (u - U_inf, _);
+//                               float4 omgm (W, _); int32 cell (home cell)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace susp {
+
+constexpr int kBlock = 256;          // threads per block of particle kernels
+constexpr int kStressComp = 3;       // contact, lubrication, pair Brownian
+constexpr int kPartialLen = 27;      // 3 components x 9 entries
+constexpr int kKinLen = 18;          // translational + rotational kinetic
+
+// error bits of Ctl::err
+constexpr int kErrNonFinite = 1;
+constexpr int kErrOverflow = 2;
+constexpr int kErrOverlap = 4;
+constexpr int kErrWrap = 8;
+
+struct Replica {
+  double L[3];
+  double rate;       // shear rate
+  double rate_dt;    // rate * dt (set per step call)
+  double kT;
+  double noise_c;    // sqrt(2 kT / dt)
+  double eta, kn, kt, mu;
+  double V;
+  double flip_at;    // 0.5 Lx / Ly
+  double flip_by;    // Lx / Ly
+  double strain;     // current strain (advanced on the device)
+  double tilt;       // strain * Ly
+  double hcell[3];   // cell extents in fractional units (1/nc)
+  uint32_t key0, key1;   // Philox key (seed)
+  int32_t nc[3];     // cell grid
+  int32_t pad0;
+  int64_t cell_base; // first cell key of this replica
+  int64_t p0, n;     // particle range (tags and sorted order)
+};
+
+struct Ctl {
+  long long k;                  // evaluation index of the forces held
+  unsigned long long vmax_bits; // max peculiar speed of this step (double bits)
+  double disp_bound;            // accumulated displacement bound D
+  double t_since_build;
+  int need_rebuild;
+  int err;
+  int cur;                      // live copy of the double-buffered arrays
+  int nbuilds;
+  int max_row;                  // longest neighbour row at the last build
+  unsigned int ticket;          // last-block detection in the integrator
+  long long npairs;             // pairs in the list
+  long long graph_steps;
+};
+
+// Per-block work map: block b handles sorted particles [start, end) of one
+// replica, so block reductions are per replica and deterministic.
+struct BlockMap {
+  const int* rep;
+  const int* start;
+  const int* end;
+  int nblocks;
+};
+
+template <typename T>
+struct Pair2 {
+  T* a[2];
+  __host__ __device__ T* operator[](int i) const { return a[i]; }
+};
+
+struct Arrays {
+  int64_t N;        // total particles
+  int64_t Npad;     // padded stride of SoA arrays
+  int kmax;
+  int R;
+  Pair2<double4_32a> pos, vel, omg;
+  Pair2<double> frc, trq;
+  Pair2<int> tag, rep;
+  Pair2<int> nbr, nnb;
+  Pair2<double> hist;
+  Pair2<unsigned long long> cmsk;
+  int* slot_of_tag;     // tag -> sorted index (live copy)
+  int* cell;            // home cell of sorted particle (new order after build)
+  float4* posm;         // mixed-precision mirrors
+  float4* velm;
+  float4* omgm;
+  // neighbour-build scratch
+  int* key;             // cell key per particle (old order)
+  int* perm;            // new sorted index -> old sorted index
+  int* cell_count;      // [ncell_total + 1]
+  int* cell_start;      // [ncell_total + 1]
+  int* cell_fill;       // [ncell_total]
+  int* scan_part;       // block sums of the scan
+  int64_t ncell;
+  // reductions
+  double* pair_partial; // [nblocks][27]
+  double* kin_partial;  // [nblocks][18]
+  double* stress_acc;   // [R][48]: 27 pair, 18 kinetic, pair / kinetic counts
+  int* rep_bstart;      // [R + 1] first block of each replica
+  Replica* repl;        // [R]
+  Ctl* ctl;
+};
+
+struct StepArgs {
+  double dt;
+  double hdt;        // dt / 2
+  double xi_min, xi_max, skin;
+  double rcmax;      // largest lubrication cutoff (a_i + a_j)(1 + xi_max/2)
+  double rate_max;   // largest |rate| over replicas
+  double torque_sign;
+  int noise, lubrication, onebody, contact, friction;
+  int advance;       // 1: time advanced since the previous evaluation
+  int sample;        // 1: accumulate stresses at this evaluation
+};
+
+// ---- host-side launchers (defined in the .cu files) ----------------------
+void launch_integrate_fp64(const Arrays& A, const BlockMap& bm,
+                           const StepArgs& s, int close, int sample_kin,
+                           cudaStream_t st, unsigned long long cond_handle,
+                           int use_cond);
+void launch_finalize_fp64(const Arrays& A, const BlockMap& bm,
+                          const StepArgs& s, int sample_kin, cudaStream_t st);
+void launch_pair_fp64(const Arrays& A, const BlockMap& bm, const StepArgs& s,
+                      int tpp, cudaStream_t st);
+void launch_integrate_mixed(const Arrays& A, const BlockMap& bm,
+                            const StepArgs& s, int close, int sample_kin,
+                            cudaStream_t st, unsigned long long cond_handle,
+                            int use_cond);
+void launch_finalize_mixed(const Arrays& A, const BlockMap& bm,
+                           const StepArgs& s, int sample_kin, cudaStream_t st);
+void launch_mirror(const Arrays& A, const BlockMap& bm, cudaStream_t st);
+void launch_pair_mixed(const Arrays& A, const BlockMap& bm, const StepArgs& s,
+                       int tpp, cudaStream_t st);
+void launch_reduce_stress(const Arrays& A, const BlockMap& bm, int sample_pair,
+                          int sample_kin, cudaStream_t st);
+// neighbour rebuild: `gated` kernels return at once unless ctl->need_rebuild
+void launch_rebuild(const Arrays& A, const BlockMap& bm, const StepArgs& s,
+                    cudaStream_t st, int mixed);
+void launch_mirror_gated_next(const Arrays& A, cudaStream_t st);
+void launch_request_rebuild(const Arrays& A, cudaStream_t st);
+void launch_load_state(const Arrays& A, const double* x, const double* U,
+                       const double* W, const double* radius,
+                       const double* mass, const double* inertia,
+                       const int* rep_of, cudaStream_t st);
+void launch_zero_forces(const Arrays& A, cudaStream_t st);
+void launch_gather(const Arrays& A, int what, double* out, cudaStream_t st);
+void launch_row_counts(const Arrays& A, int with_history, long long* cnt,
+                       cudaStream_t st);
+void launch_list_pairs(const Arrays& A, const long long* off, int* ij,
+                       int with_history, double* xi_t, cudaStream_t st);
+
+}  // namespace susp
