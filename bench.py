@@ -1,0 +1,399 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 suspension stepper in particle-steps/s.
+
+Workload: 1,000,000 bidisperse spheres (radii 1 and 1.4, equal numbers),
+volume fraction 0.58, Pe = 1000, friction coefficient 1 (k_t = k_n / 2),
+k_n = 1e4, dt = 1e-4, skin 0.3, mixed precision (single-precision pair
+arithmetic on gaps formed from double positions; double integration, history
+and stress).  One bench step = one library call advancing `--inner`
+timesteps (kick/drift/wrap, neighbour rebuilds when due, pair forces, stress
+reduction), so every row of the hot path runs inside the timed region.
+
+value: N * inner * steps / (device time of the timed steps), inputs resident
+in HBM; e2e: the same metric through the public API with the state uploaded
+from pinned host memory and the stress read back every step.  The roofline
+entry covers the kernel family that takes most device time, timed with CUDA
+events on the library's stream in a profiling pass right after the timed
+steps.  Under torchrun each rank steps its own independent system (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+
+--impl reference times the plain FP64 CPU oracle on a bounded sample of the
+same workload instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "bidisperse-1M-phi0.58-pe1000-mu1"
+METRIC = "particle-steps/s"
+
+# DRAM traffic per launch of the dominant kernel from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), recorded per sphere together
+# with the hash of the source it was taken on; reported only while the
+# source is unchanged.  Filled from profiles/.
+NCU_TRAFFIC = {}
+
+
+def _src_hash(name: str) -> str:
+    path = os.path.join(ROOT, "paper_2307_13802_gb300", "csrc", name)
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--inner", type=int, default=100,
+                    help="timesteps advanced per bench step")
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the FP64-path comparison line")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.tmp.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.tmp.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per sphere of each kernel family
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(family: str, precision: str, K: float, c: float, fric: bool) -> float:
+    """Bytes each launch must move per sphere: every record read or written
+    once, gathers of neighbours not counted again, atomics counted as one
+    write of the accumulator.  K = half-list slots per sphere, c = touching
+    pairs with history per sphere."""
+    hist = (16.0 + 48.0 * c) if fric else 0.0
+    if family == "pair":
+        if precision == "mixed":
+            # own mirrors: double-float offset+radius (32), velocity+tag (16),
+            # spin+cell (16); row length (4) + list 4K; float4 force and
+            # torque accumulation (32); contact mask / history
+            return 64.0 + 4.0 + 4.0 * K + 32.0 + hist
+        # x, U, W records (96) + tag, row length (8) + list 4K + force and
+        # torque accumulation (48) + contact mask / history
+        return 96.0 + 8.0 + 4.0 * K + 48.0 + hist
+    if family == "integrate":
+        if precision == "mixed":
+            # read x, U, W (96) + float4 F, T (32) + cell, tag (8); write
+            # x, U, W (96) + mirrors (64) + cleared F, T (32)
+            return 96.0 + 32.0 + 8.0 + 96.0 + 64.0 + 32.0
+        # read x, U, W (96) + F, T (48); write x, U, W (96) + cleared F, T (48)
+        return 96.0 + 48.0 + 96.0 + 48.0
+    if family == "finalize":
+        return 32.0 + 32.0 + 48.0 + 32.0 + 32.0
+    return 0.0
+
+
+def run_ours(args, rank, world, local_rank, dist):
+    import numpy as np
+    import torch
+
+    import paper_2307_13802_gb300 as susp
+    import workloads
+
+    torch.cuda.set_device(local_rank)
+    w = workloads.named(WORKLOAD)
+    if world > 1:
+        # independent replica per rank: a different dynamics seed
+        w.params["seed"] = w.params["seed"] + 7919 * rank
+    p = w.params
+    N = w.N
+    stream = torch.cuda.Stream()
+
+    def make(precision):
+        s = susp.System(w.radii, w.box, precision=precision, eta=p["eta"], rho=p["rho"],
+                        kn=p["kn"], kt=p["kt"], mu=p["mu"], skin=p["skin"],
+                        shear_rate=p["shear_rate"], kT=p["kT"], seed=p["seed"], dt=p["dt"])
+        s.set_stream(stream.cuda_stream)
+        s.set_state(w.x, w.U, w.W)
+        return s
+
+    def step(s, n):
+        s.step(n, p["shear_rate"], p["kT"], p["dt"], p["seed"])
+
+    sysm = make(args.precision)
+    for _ in range(args.warmup):
+        step(sysm, args.inner)
+    sysm.stress()
+    info0 = sysm.info()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(sysm, args.inner)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    info1 = sysm.info()
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    sig = sysm.stress()
+    value = world * N * args.inner * args.steps / (ms / 1e3)
+
+    # where the time goes: per-family device time over one more bench step
+    prof = sysm.profile(args.inner, p["dt"])
+    info = sysm.info()
+    ij, _ = sysm.history()
+    K = info["npairs"] / N
+    c = len(ij) / N
+    fric = p["mu"] > 0
+    fam = max(("integrate", "pair", "rebuild", "finalize", "reduce"),
+              key=lambda f: prof[f]["ms"])
+    hbm, peak_kind = peaks()
+    per_sphere = algorithmic_bytes(fam, args.precision, K, c, fric)
+    roofline = None
+    if per_sphere > 0 and prof[fam]["launches"] > 0:
+        bytes_per_launch = per_sphere * N
+        achieved = bytes_per_launch / (prof[fam]["ms_per_launch"] * 1e-3) / 1e9
+        kernel = {"pair": "k_pair_mixed" if args.precision == "mixed" else "k_pair_fp64",
+                  "integrate": "k_integrate_mixed" if args.precision == "mixed" else "k_integrate_fp64",
+                  "finalize": "k_finalize"}.get(fam, fam)
+        src = "k_mixed.cu" if args.precision == "mixed" else (
+            "k_pair_fp64.cu" if fam == "pair" else "k_integrate_fp64.cu")
+        rec = NCU_TRAFFIC.get(kernel)
+        traffic = None
+        if rec and rec.get("source_sha") == _src_hash(src):
+            traffic = rec["bytes_per_sphere"] * N
+        roofline = {"bound": "hbm", "kernel": kernel, "achieved": round(achieved, 1),
+                    "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                    "frac": round(achieved / hbm, 4), "traffic": traffic,
+                    "algorithmic_bytes_per_launch": bytes_per_launch,
+                    "bytes_per_sphere": per_sphere,
+                    "ms_per_launch": prof[fam]["ms_per_launch"],
+                    "half_list_slots_per_sphere": round(K, 3),
+                    "contacts_per_sphere": round(c, 3)}
+    breakdown = {f: {"ms_per_launch": round(v["ms_per_launch"], 5),
+                     "launches": v["launches"], "ms": round(v["ms"], 3)}
+                 for f, v in prof.items()}
+
+    # end to end: pinned host state in, stress out, every bench step
+    x, U, Wv = sysm.state()
+    pin = [torch.empty((N, 3), dtype=torch.float64, pin_memory=True) for _ in range(3)]
+    for dst, src in zip(pin, (x, U, Wv)):
+        dst.numpy()[:] = src
+    hx, hU, hW = (t.numpy() for t in pin)
+    e2e_steps = max(3, args.steps // 4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sysm.set_state(hx, hU, hW)
+        step(sysm, args.inner)
+        st = sysm.stress()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = world * N * args.inner * e2e_steps / e2e_s
+    assert math.isfinite(st["eta_r"])
+
+    fp64 = None
+    if not args.no_fp64 and args.precision == "mixed":
+        s64 = make("fp64")
+        step(s64, 4)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        n64 = 20
+        e0.record(stream)
+        step(s64, n64)
+        e1.record(stream)
+        e1.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        fp64 = {"value": round(world * N * n64 / (ms64 / 1e3), 1),
+                "ms_per_timestep": round(ms64 / n64, 4),
+                "speedup_of_mixed": round(value / (world * N * n64 / (ms64 / 1e3)), 2)}
+        s64.close()
+
+    launches = int(info1["launches"] - info0["launches"])
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": METRIC,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32-pair/f64-state"
+        if args.precision == "mixed" else "f64",
+        "data": "synthetic seeded packing (no dataset)",
+        "config": {"workload": WORKLOAD, "N": N, "phi": 0.58, "Pe": 1000.0, "mu": 1.0,
+                   "precision": args.precision, "timesteps_per_step": args.inner,
+                   "dt": p["dt"], "box": round(w.L, 4), "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (state + list > 300 MB)"},
+        "e2e": {"value": round(e2e_val, 1), "unit": METRIC,
+                "h2d_bytes_per_step": 3 * 3 * 8 * N, "d2h_bytes_per_step": 58 * 8},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "kernel_breakdown": breakdown,
+        "eta_r": round(float(sig["eta_r"]), 4),
+        "neighbour_builds": int(info1["nbuilds"] - info0["nbuilds"]),
+    }
+    if fp64:
+        out["fp64_path"] = fp64
+    if clk:
+        out["clocks"] = clk
+    return out
+
+
+def cpu_sample_workload():
+    """Bounded sample of the workload: the 15,625-sphere periodic tile from
+    which the 1M packing is replicated (same seeds, phi, Pe, mu)."""
+    import workloads
+    c = workloads.WORKLOADS[WORKLOAD]
+    ps, ds = c["seeds"]
+    return workloads.make(15625, c["phi"], c["pe"], c["mu"], poly=c["poly"],
+                          pack_seed=ps, dyn_seed=ds)
+
+
+def run_cpu_baseline(timesteps: int = 400):
+    import oracle
+    w = cpu_sample_workload()
+    o = oracle.System(w.radii, w.box, **w.params)
+    o.set_state(w.x, w.U, w.W)
+    o.step(1)                       # list build and setup evaluation
+    t0 = time.perf_counter()
+    o.step(timesteps)
+    dt = time.perf_counter() - t0
+    return {"value": round(w.N * timesteps / dt, 1), "unit": METRIC, "cores": 1,
+            "kind": "oracle",
+            "sample": f"{w.N}-sphere periodic tile of the same packing recipe, "
+                      f"{timesteps} timesteps, serial FP64 oracle with O(N^2) list builds"}
+
+
+def run_reference(args):
+    import oracle
+    w = cpu_sample_workload()
+    o = oracle.System(w.radii, w.box, **w.params)
+    o.set_state(w.x, w.U, w.W)
+    inner = 20
+    o.step(1)
+    for _ in range(args.warmup):
+        o.step(inner)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(inner)
+    dt = time.perf_counter() - t0
+    value = w.N * inner * args.steps / dt
+    sample = (f"{w.N}-sphere periodic tile of the {WORKLOAD} packing, {inner} timesteps "
+              f"per bench step, serial FP64 oracle")
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": METRIC,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic seeded packing (no dataset)",
+            "config": {"workload": WORKLOAD, "N": w.N, "timesteps_per_step": inner,
+                       "parallelism": "cpu"},
+            "cpu_baseline": {"value": round(value, 1), "unit": METRIC, "cores": 1,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 1), "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(local_rank)
+        td.init_process_group("nccl")
+        dist = td
+    out = run_ours(args, rank, world, local_rank, dist)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = run_cpu_baseline()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

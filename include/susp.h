@@ -186,6 +186,18 @@ int susp_step(susp_t* h, int64_t n_steps, double shear_rate, double kT,
  * per-replica rate, kT and seed given at creation. */
 int susp_step_batch(susp_t* h, int64_t n_steps, double dt);
 
+/* Measures where the time goes: advances n_steps exactly as
+ * susp_step()/susp_step_batch() would (same physics, the parameters of the
+ * last step call), but launches every kernel eagerly between two CUDA events
+ * recorded on the handle's stream, and a neighbour rebuild only when it is
+ * due.  out[SUSP_PROFILE_LEN] holds, for each kernel family f -- 0 integrator
+ * (kick, drift, wrap), 1 neighbour rebuild (binning, sort, list, history),
+ * 2 pair forces, 3 stress reduction, 4 closing half kick --
+ * out[3f] the total device milliseconds, out[3f+1] the number of launches and
+ * out[3f+2] the mean milliseconds per launch. */
+#define SUSP_PROFILE_LEN 15
+int susp_profile(susp_t* h, int64_t n_steps, double dt, double* out);
+
 /* Stress of replica `replica` averaged over the sampled evaluations since
  * the previous call (which it resets).  out[SUSP_STRESS_LEN]:
  *   [ 0.. 8] contact        sigma^C  (row-major 3x3, Sec. II.A)
@@ -214,8 +226,10 @@ int susp_get_history(susp_t* h, int32_t* ij, double* xi_t, int64_t cap,
  * [2] longest row at the last build, [3] row capacity, [4] pairs in the
  * list, [5] strain of replica 0, [6] tilt of replica 0, [7] threads per
  * particle in use, [8] precision, [9] replicas, [10] total spheres,
- * [11] steps replayed through graphs, [12] device bytes held. */
-#define SUSP_INFO_LEN 13
+ * [11] steps replayed through graphs, [12] device bytes held, [13] kernels
+ * launched so far (eager launches, graph kernel nodes per replay, and the
+ * kernels of each rebuild taken inside a replay). */
+#define SUSP_INFO_LEN 14
 int susp_get_info(susp_t* h, double* info);
 
 /* ---- checkpoint ------------------------------------------------------------- */

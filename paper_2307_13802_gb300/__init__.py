@@ -20,7 +20,9 @@ SUSP_OK, SUSP_EINVAL, SUSP_ENOMEM, SUSP_ECUDA, SUSP_ESTATE = 0, 1, 2, 3, 4
 SUSP_ENEIGH, SUSP_EUNSTABLE, SUSP_ETIMEOUT, SUSP_ENODEV = 5, 6, 7, 8
 SUSP_FP64, SUSP_MIXED = 0, 1
 SUSP_STRESS_LEN = 58
-SUSP_INFO_LEN = 13
+SUSP_INFO_LEN = 14
+SUSP_PROFILE_LEN = 15
+PROFILE_FAMILIES = ("integrate", "rebuild", "pair", "reduce", "finalize")
 
 ERROR_NAMES = {0: "SUSP_OK", 1: "SUSP_EINVAL", 2: "SUSP_ENOMEM", 3: "SUSP_ECUDA",
                4: "SUSP_ESTATE", 5: "SUSP_ENEIGH", 6: "SUSP_EUNSTABLE",
@@ -76,6 +78,7 @@ _SIGNATURES = {
                             C.c_uint64]),
     "susp_step_batch": (C.c_int, [_H, C.c_int64, C.c_double]),
     "susp_stress": (C.c_int, [_H, C.c_int32, _D]),
+    "susp_profile": (C.c_int, [_H, C.c_int64, C.c_double, _D]),
     "susp_get_pairs": (C.c_int, [_H, _I32, C.c_int64, _I64]),
     "susp_get_history": (C.c_int, [_H, _I32, _D, C.c_int64, _I64]),
     "susp_get_info": (C.c_int, [_H, _D]),
@@ -223,6 +226,13 @@ class System:
     def step_batch(self, n: int, dt: float):
         self._chk(lib.susp_step_batch(self._h, int(n), float(dt)))
 
+    def profile(self, n: int, dt: float) -> dict:
+        """Per kernel family: total ms, launches, mean ms per launch."""
+        out = np.zeros(SUSP_PROFILE_LEN)
+        self._chk(lib.susp_profile(self._h, int(n), float(dt), _dp(out)))
+        return {f: dict(ms=out[3 * i], launches=int(out[3 * i + 1]), ms_per_launch=out[3 * i + 2])
+                for i, f in enumerate(PROFILE_FAMILIES)}
+
     def stress(self, replica: int = 0) -> dict:
         out = np.zeros(SUSP_STRESS_LEN)
         self._chk(lib.susp_stress(self._h, int(replica), _dp(out)))
@@ -253,7 +263,7 @@ class System:
         self._chk(lib.susp_get_info(self._h, _dp(out)))
         keys = ("k", "nbuilds", "max_row", "kmax", "npairs", "strain", "tilt",
                 "threads_per_particle", "precision", "replicas", "N",
-                "graph_steps", "device_bytes")
+                "graph_steps", "device_bytes", "launches")
         return dict(zip(keys, out.tolist()))
 
     def save(self, path: str):

@@ -28,6 +28,7 @@ UNITS = [
     ("k_neighbors.cu", ["-fmad=false"]),
     ("k_util.cu", ["-fmad=false"]),
     ("k_mixed.cu", ["-fmad=true"]),
+    ("k_pair_mixed.cu", ["-fmad=true", "-prec-div=false", "-prec-sqrt=false"]),
 ]
 
 

@@ -24,6 +24,7 @@ thread_local std::string g_create_error;
 struct GraphChunk {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  int64_t kernels = 0;  // kernel nodes outside the conditional rebuild bodies
 };
 
 }  // namespace
@@ -69,6 +70,15 @@ struct susp_s {
   uint64_t cur_seed = 0;
   bool seed_set = false;
   int64_t graph_steps = 0;
+  int64_t launches = 0;            // kernels enqueued (eager + graph replays)
+  int64_t capture_launches = 0;    // kernels in the graph being captured
+  int last_nbuilds = 0;
+  int last_nbuilds_seen = 0;
+  // profiling: events around each launch, summed per kernel family
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_marks;
   std::map<int64_t, GraphChunk> graphs;
   cudaStream_t side = nullptr;
   cudaStream_t own_stream = nullptr;
@@ -116,7 +126,7 @@ int validate_params(const susp_params* p, std::string& msg) {
   if (!(p->skin >= 0)) { msg = "skin must be >= 0"; return SUSP_EINVAL; }
   if (!(p->kT >= 0)) { msg = "kT must be >= 0"; return SUSP_EINVAL; }
   if (!(p->dt > 0) || !std::isfinite(p->dt)) { msg = "dt must be > 0"; return SUSP_EINVAL; }
-  if (!std::isfinite(p->shear_rate)) { msg = "shear rate must be finite"; return SUSP_EINVAL; }
+  if (!(p->shear_rate >= 0) || !std::isfinite(p->shear_rate)) { msg = "shear rate must be finite and >= 0"; return SUSP_EINVAL; }
   if (p->precision != SUSP_FP64 && p->precision != SUSP_MIXED) {
     msg = "precision must be SUSP_FP64 or SUSP_MIXED"; return SUSP_EINVAL;
   }
@@ -214,6 +224,11 @@ int common_create(susp_t** out, int32_t R, const int64_t* N_r,
     Rr.nc[0] = (int)std::floor(wx / guard);
     Rr.nc[1] = (int)std::floor(Rr.L[1] / guard);
     Rr.nc[2] = (int)std::floor(Rr.L[2] / guard);
+    if (Rr.nc[0] > 1023 || Rr.nc[1] > 1023 || Rr.nc[2] > 1023) {
+      delete h;
+      g_create_error = "more than 1023 cells along a box edge";
+      return SUSP_EINVAL;
+    }
     if (Rr.nc[0] < 3 || Rr.nc[1] < 3 || Rr.nc[2] < 3) {
       delete h;
       char buf[256];
@@ -295,6 +310,7 @@ int allocate(susp_t* h) {
   A.kmax = h->kmax;
   A.R = h->R;
   A.ncell = h->ncell;
+  A.mixed = h->p0.precision == SUSP_MIXED ? 1 : 0;
   const int64_t Np = h->Npad;
   const bool fric = true;  // history arrays are cheap to hold; used when mu > 0
   bool ok = true;
@@ -322,13 +338,14 @@ int allocate(susp_t* h) {
   ok &= alloc_n(h, &A.scan_part, nparts + 1);
   const int nb = (int)h->bm_rep.size();
   ok &= alloc_n(h, &A.pair_partial, (int64_t)nb * kPartialLen);
+  ok &= alloc_n(h, &A.pair_partial_w, (int64_t)nb * kPartialLen);
   ok &= alloc_n(h, &A.kin_partial, (int64_t)nb * kKinLen);
   ok &= alloc_n(h, &A.stress_acc, (int64_t)h->R * 48);
   ok &= alloc_n(h, &A.rep_bstart, h->R + 1);
   ok &= alloc_n(h, &A.repl, h->R);
   ok &= alloc_n(h, &A.ctl, 1);
   if (h->p0.precision == SUSP_MIXED) {
-    ok &= alloc_n(h, &A.posm, Np);
+    ok &= alloc_n(h, &A.posm, 2 * Np);  // 32-byte (hi, lo) records
     ok &= alloc_n(h, &A.velm, Np);
     ok &= alloc_n(h, &A.omgm, Np);
   }
@@ -390,6 +407,11 @@ StepArgs make_args(const susp_t* h, double dt, int advance, int sample) {
   s.friction = fric;
   s.advance = advance;
   s.sample = sample;
+  s.dt_f = (float)s.dt;
+  s.hdt_f = (float)s.hdt;
+  s.xi_min_f = (float)s.xi_min;
+  s.xi_max_f = (float)s.xi_max;
+  s.tsign_f = (float)s.torque_sign;
   return s;
 }
 
@@ -406,6 +428,7 @@ int sync_replicas(susp_t* h, double dt) {
     R.tilt = dev[r].tilt;
     R.rate_dt = R.rate * dt;
     R.noise_c = std::sqrt(2.0 * R.kT / dt);
+    refresh_constant_fields(R);
   }
   CK(cudaMemcpyAsync(h->A.repl, h->repl_h.data(), sizeof(Replica) * h->R,
                      cudaMemcpyHostToDevice, h->stream));
@@ -425,6 +448,7 @@ int check_errors(susp_t* h) {
   CK(cudaMemcpyAsync(&c, h->A.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaGetLastError());
+  h->last_nbuilds_seen = c.nbuilds;
   if (c.err) {
     int e = c.err;
     int zero = 0;
@@ -443,27 +467,67 @@ int check_errors(susp_t* h) {
   return SUSP_OK;
 }
 
+// kernel families reported by susp_profile()
+enum { kFamIntegrate = 0, kFamRebuild = 1, kFamPair = 2, kFamReduce = 3,
+       kFamFinalize = 4, kFamCount = 5 };
+
+cudaEvent_t next_event(susp_t* h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[h->ev_used++];
+}
+
+// Runs f() (which enqueues kernels on st); in profiling mode brackets it
+// with events charged to `family`.
+template <class Fn>
+void timed(susp_t* h, int family, cudaStream_t st, Fn&& f) {
+  if (!h->profiling) { f(); return; }
+  cudaEvent_t a = next_event(h), b = next_event(h);
+  cudaEventRecord(a, st);
+  f();
+  cudaEventRecord(b, st);
+  h->ev_marks.push_back({family, {a, b}});
+}
+
 void launch_integrate(susp_t* h, const StepArgs& s, int close, int sample_kin,
                       unsigned long long cond, int use_cond, cudaStream_t st) {
-  if (h->p0.precision == SUSP_MIXED)
-    launch_integrate_mixed(h->A, h->bm, s, close, sample_kin, st, cond, use_cond);
-  else
-    launch_integrate_fp64(h->A, h->bm, s, close, sample_kin, st, cond, use_cond);
+  timed(h, kFamIntegrate, st, [&] {
+    if (h->p0.precision == SUSP_MIXED)
+      launch_integrate_mixed(h->A, h->bm, s, close, sample_kin, st, cond, use_cond);
+    else
+      launch_integrate_fp64(h->A, h->bm, s, close, sample_kin, st, cond, use_cond);
+  });
 }
 
 void launch_pair(susp_t* h, const StepArgs& s, cudaStream_t st) {
-  if (h->p0.precision == SUSP_MIXED) {
-    launch_pair_mixed(h->A, h->bm, s, h->tpp, st);
-  } else {
-    launch_pair_fp64(h->A, h->bm, s, h->tpp, st);
-  }
+  timed(h, kFamPair, st, [&] {
+    if (h->p0.precision == SUSP_MIXED)
+      launch_pair_mixed(h->A, h->bm, s, h->tpp, st);
+    else
+      launch_pair_fp64(h->A, h->bm, s, h->tpp, st);
+  });
 }
 
 void launch_finalize(susp_t* h, const StepArgs& s, int sample_kin, cudaStream_t st) {
-  if (h->p0.precision == SUSP_MIXED)
-    launch_finalize_mixed(h->A, h->bm, s, sample_kin, st);
-  else
-    launch_finalize_fp64(h->A, h->bm, s, sample_kin, st);
+  timed(h, kFamFinalize, st, [&] {
+    if (h->p0.precision == SUSP_MIXED)
+      launch_finalize_mixed(h->A, h->bm, s, sample_kin, st);
+    else
+      launch_finalize_fp64(h->A, h->bm, s, sample_kin, st);
+  });
+}
+
+void launch_reduce(susp_t* h, int sample_pair, int sample_kin, cudaStream_t st) {
+  if (!sample_pair && !sample_kin) return;
+  timed(h, kFamReduce, st, [&] { launch_reduce_stress(h->A, h->bm, sample_pair, sample_kin, st); });
+}
+
+// kernels in one neighbour rebuild (gated sequence of k_neighbors.cu)
+int rebuild_kernels(const susp_t* h, const StepArgs& s) {
+  return 11 + (s.friction ? 1 : 0) + (h->p0.precision == SUSP_MIXED ? 1 : 0);
 }
 
 // Setup evaluation (time not advanced): rebuild if due, clear, evaluate.
@@ -473,7 +537,7 @@ void enqueue_setup_eval(susp_t* h, double dt, int sample, cudaStream_t st) {
   if (h->p0.precision == SUSP_MIXED) launch_mirror(h->A, h->bm, st);
   launch_zero_forces(h->A, st);
   launch_pair(h, s, st);
-  launch_reduce_stress(h->A, h->bm, sample, 0, st);
+  launch_reduce(h, sample, 0, st);
 }
 
 bool sampled(const susp_t* h, int64_t step_index) {
@@ -520,16 +584,31 @@ void enqueue_steps(susp_t* h, int64_t first, int64_t n, double dt,
       cudaStreamBeginCaptureToGraph(h->side, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
       launch_rebuild(h->A, h->bm, s, h->side, h->p0.precision == SUSP_MIXED);
       cudaStreamEndCapture(h->side, &body);
+    } else if (h->profiling) {
+      // profiling: launch the rebuild only when it is due, so that its
+      // events time real work
+      int need = 0;
+      cudaMemcpyAsync(&need, &h->A.ctl->need_rebuild, sizeof(int), cudaMemcpyDeviceToHost, st);
+      cudaStreamSynchronize(st);
+      if (need) {
+        timed(h, kFamRebuild, st, [&] {
+          launch_rebuild(h->A, h->bm, s, st, h->p0.precision == SUSP_MIXED);
+        });
+        h->launches += rebuild_kernels(h, s);
+      }
     } else {
       launch_rebuild(h->A, h->bm, s, st, h->p0.precision == SUSP_MIXED);
+      h->launches += rebuild_kernels(h, s);  // gated: launched every step
     }
     launch_pair(h, s, st);
-    launch_reduce_stress(h->A, h->bm, samp, skin_prev, st);
+    launch_reduce(h, samp, skin_prev, st);
+    (capture ? h->capture_launches : h->launches) += 2 + ((samp || skin_prev) ? 1 : 0);
   }
   StepArgs s = make_args(h, dt, 1, 0);
   const int last_kin = sampled(h, first + n - 1);
   launch_finalize(h, s, last_kin, st);
-  launch_reduce_stress(h->A, h->bm, 0, last_kin, st);
+  launch_reduce(h, 0, last_kin, st);
+  (capture ? h->capture_launches : h->launches) += 1 + (last_kin ? 1 : 0);
 }
 
 int get_graph(susp_t* h, int64_t n, double dt, GraphChunk** out) {
@@ -538,6 +617,7 @@ int get_graph(susp_t* h, int64_t n, double dt, GraphChunk** out) {
   if (!h->side) CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
   GraphChunk gc;
   std::vector<unsigned long long> conds;
+  h->capture_launches = 0;
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   enqueue_steps(h, 0, n, dt, h->stream, true, &conds);
   cudaError_t e = cudaStreamEndCapture(h->stream, &gc.graph);
@@ -551,6 +631,7 @@ int get_graph(susp_t* h, int64_t n, double dt, GraphChunk** out) {
     cudaGraphDestroy(gc.graph);
     return fail(h, SUSP_ECUDA, std::string("graph instantiation failed: ") + cudaGetErrorString(e));
   }
+  gc.kernels = h->capture_launches;
   h->graphs[n] = gc;
   *out = &h->graphs[n];
   return SUSP_OK;
@@ -572,6 +653,7 @@ int run_steps(susp_t* h, int64_t n_steps, double dt) {
   }
   const int64_t chunk = 32;
   int64_t done = 0;
+  bool graph_used = false;
   while (done < n_steps) {
     const int64_t left = n_steps - done;
     const bool graphs_ok = h->p0.use_graphs && (chunk % h->p0.sample_every == 0);
@@ -586,6 +668,8 @@ int run_steps(susp_t* h, int64_t n_steps, double dt) {
         continue;
       }
       CK(cudaGraphLaunch(g->exec, st));
+      h->launches += g->kernels;
+      graph_used = true;
       done += chunk;
       h->steps_done += chunk;
       h->graph_steps += chunk;
@@ -595,7 +679,14 @@ int run_steps(susp_t* h, int64_t n_steps, double dt) {
       h->steps_done += left;
     }
   }
-  return check_errors(h);
+  rc = check_errors(h);
+  if (graph_used) {
+    // rebuilds taken inside graph replays ran the conditional body
+    h->launches += (int64_t)(h->last_nbuilds_seen - h->last_nbuilds) *
+                   rebuild_kernels(h, make_args(h, dt, 1, 0));
+  }
+  h->last_nbuilds = h->last_nbuilds_seen;
+  return rc;
 }
 
 int gather_host(susp_t* h, int what, double* out) {
@@ -705,6 +796,7 @@ void susp_destroy(susp_t* h) {
   cudaSetDevice(h->dev);
   if (h->allocated) cudaStreamSynchronize(h->stream);
   release_all(h);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   delete h;
 }
@@ -758,7 +850,8 @@ static int set_state_impl(susp_t* h, const double* x, const double* U, const dou
   // strain/tilt must be current before wrapping
   rc = sync_replicas(h, h->last_dt);
   if (rc) return rc;
-  launch_load_state(h->A, dx, dU, dW, h->d_radius, h->d_mass, h->d_inertia, h->d_rep_of,
+  (h->p0.precision == SUSP_MIXED ? launch_load_state_mixed : launch_load_state)(
+      h->A, dx, dU, dW, h->d_radius, h->d_mass, h->d_inertia, h->d_rep_of,
                     h->stream);
   launch_request_rebuild(h->A, h->stream);
   h->have_state = true;
@@ -787,6 +880,7 @@ int susp_set_clock(susp_t* h, int64_t k, int32_t replica, double strain) {
     if (!(std::fabs(strain) <= R.flip_at)) return fail(h, SUSP_EINVAL, "strain out of range");
     R.strain = strain;
     R.tilt = strain * R.L[1];
+    refresh_strain_fields(R);
   }
   CK(cudaMemcpyAsync(h->A.repl, h->repl_h.data(), sizeof(Replica) * h->R,
                      cudaMemcpyHostToDevice, h->stream));
@@ -844,7 +938,7 @@ int susp_step(susp_t* h, int64_t n_steps, double shear_rate, double kT, double d
   if (!h) return SUSP_EINVAL;
   h->err.clear();
   if (h->R != 1) return fail(h, SUSP_EINVAL, "batch handles step with susp_step_batch()");
-  if (!(kT >= 0) || !std::isfinite(shear_rate))
+  if (!(kT >= 0) || !(shear_rate >= 0) || !std::isfinite(shear_rate))
     return fail(h, SUSP_EINVAL, "need kT >= 0 and a finite shear rate");
   Replica& R = h->repl_h[0];
   if (R.rate != shear_rate || R.kT != kT || R.key0 != (uint32_t)(seed & 0xffffffffull) ||
@@ -870,6 +964,35 @@ int susp_step_batch(susp_t* h, int64_t n_steps, double dt) {
   h->err.clear();
   if (dt != h->last_dt && h->last_dt > 0) h->forces_valid = false;
   return run_steps(h, n_steps, dt);
+}
+
+int susp_profile(susp_t* h, int64_t n_steps, double dt, double* out) {
+  if (!h || !out) return SUSP_EINVAL;
+  h->err.clear();
+  const int graphs = h->p0.use_graphs;
+  h->p0.use_graphs = 0;
+  h->profiling = true;
+  h->ev_used = 0;
+  h->ev_marks.clear();
+  int rc = run_steps(h, n_steps, dt);
+  h->profiling = false;
+  h->p0.use_graphs = graphs;
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(h->stream));
+  double ms[kFamCount] = {0, 0, 0, 0, 0}, cnt[kFamCount] = {0, 0, 0, 0, 0};
+  for (auto& m : h->ev_marks) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, m.second.first, m.second.second));
+    ms[m.first] += t;
+    cnt[m.first] += 1;
+  }
+  h->ev_marks.clear();
+  for (int f = 0; f < kFamCount; ++f) {
+    out[3 * f] = ms[f];
+    out[3 * f + 1] = cnt[f];
+    out[3 * f + 2] = cnt[f] > 0 ? ms[f] / cnt[f] : 0.0;
+  }
+  return SUSP_OK;
 }
 
 int susp_stress(susp_t* h, int32_t replica, double* out) {
@@ -926,6 +1049,7 @@ int susp_get_info(susp_t* h, double* info) {
   info[10] = (double)h->N;
   info[11] = (double)h->graph_steps;
   info[12] = (double)h->bytes;
+  info[13] = (double)h->launches;
   if (!h->allocated) return SUSP_OK;
   CK(cudaSetDevice(h->dev));
   Ctl c{};

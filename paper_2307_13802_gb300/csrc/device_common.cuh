@@ -211,4 +211,35 @@ __device__ __forceinline__ double atomic_add_f64(double* a, double v) {
   return atomicAdd(a, v);
 }
 
+// Layout-independent reads of the live state as doubles (x, y, z, a),
+// (U, m or 1/I) and (W, I): the FP64 layout is read directly, the
+// double-float halves of the mixed layout are summed.
+__device__ __forceinline__ double4_32a read_rec_d(const double4_32a* base, int mixed,
+                                                  int64_t p) {
+  if (!mixed) return base[p];
+  const float4* r = reinterpret_cast<const float4*>(base + p);
+  const float4 h = r[0], l = r[1];
+  return make_double4_32a((double)h.x + (double)l.x, (double)h.y + (double)l.y,
+                          (double)h.z + (double)l.z, (double)h.w);
+}
+
+// Force / torque of sphere p as doubles in either layout.
+__device__ __forceinline__ void read_vec3_d(const double* base, int mixed,
+                                            int64_t Np, int64_t p, double* v) {
+  if (!mixed) {
+    v[0] = base[p]; v[1] = base[Np + p]; v[2] = base[2 * Np + p];
+  } else {
+    const float4 f = reinterpret_cast<const float4*>(base)[p];
+    v[0] = f.x; v[1] = f.y; v[2] = f.z;
+  }
+}
+
+// Vector reduction of a float4 into global memory (16-byte aligned).
+__device__ __forceinline__ void red_add_v4(float4* addr, float a, float b, float c,
+                                           float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a),
+               "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+
 }  // namespace susp

@@ -1,85 +1,126 @@
-// k_mixed.cu -- mixed-precision form of the time update and of the pair
-// force evaluation.
+// k_mixed.cu -- time update and state handling of the mixed-precision path.
 //
-// Positions, velocities, spins, the tangential history and all stress and
-// force accumulators stay in double precision.  The pair arithmetic of
-// Sec. II.A-II.C (gap, resistances, lubrication, pair noise, contact) runs in
-// single precision on mirrors the integrator writes each step:
-//   posm = (x - O_home, a): offset of the sphere from the lab position of its
-//          home cell's origin O_home = H(t) s_cell (H the tilted box matrix),
-//          taken at the nearest periodic image, so |offset| stays below a
-//          few cell widths and its single-precision rounding is ~1e-7 of a
-//          radius;
-//   velm = U - U_inf(y): velocity relative to the imposed flow;
-//   omgm = Omega.
-// The separation of a listed pair is rebuilt as
-//   r = (posm_q - posm_p) + H(t) (c_q - c_p) / nc
-// with the cell difference wrapped to {-1, 0, 1}: both terms are of order
-// one cell, so the gap h = |r| - (a_i + a_j) keeps ~1e-7 absolute accuracy
-// however large the box.  The relative velocity of the image of j is
-// u_j - u_i + rate r_y x (the imposed flow difference across r), which
-// includes the Lees-Edwards image velocity without a separate shift.
+// The state (positions, velocities, spins) is held in double-float form
+// (dfloat.cuh) and advanced with FP32 instructions only: the same fused
+// Velocity-Verlet step as the FP64 path (close the previous step with
+// dt/2 F/m, open the next, drift, advance the strain with the flip of
+// Sec. II.E, wrap with the Lees-Edwards shift), with forces read from the
+// float4 accumulators the pair kernel fills.  Each step also writes the
+// single-precision mirrors the pair kernel reads:
+//   posm = (x - O_home, a) as a 32-byte double-float record (hi half, lo
+//          half): offset from the lab position of the sphere's home cell
+//          origin O_home = H(t) s_cell (H the tilted box matrix) at the
+//          nearest periodic image.  Offsets are a few cell widths at most, so
+//          the pair kernel rebuilds separations and the gap
+//          h = (d^2 - S^2)/(d + S) to ~1e-12 for any box size;
+//   velm = (U - U_inf(y), tag): velocity relative to the imposed flow;
+//   omgm = (Omega, home cell coordinates packed 10 bits per axis).
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
-#include "philox.cuh"
+#include "dfloat.cuh"
 #include "susp_internal.h"
 
 namespace susp {
 
-__device__ __forceinline__ double next_strain_m(const Replica& R) {
-  double st = R.strain + R.rate_dt;
-  if (st > R.flip_at) st = st - R.flip_by;
-  return st;
+struct DF3 {
+  df x, y, z;
+};
+
+// One 32-byte record = two float4 halves (hi, lo); w / wl are the 4th words.
+__device__ __forceinline__ void load_df3(const double4_32a* base, int64_t p, DF3& v,
+                                         float& w, float* wl = nullptr) {
+  const float4* r = reinterpret_cast<const float4*>(base + p);
+  const float4 h = r[0], l = r[1];
+  v.x = df{h.x, l.x};
+  v.y = df{h.y, l.y};
+  v.z = df{h.z, l.z};
+  w = h.w;
+  if (wl) *wl = l.w;
 }
 
-// Offset of a sphere from its home-cell origin at the nearest image, in the
-// box of tilt `tilt`; `cellkey` is the global cell key.
-__device__ __forceinline__ float4 make_posm(const Replica& R, double tilt,
-                                            int cellkey, double x, double y,
-                                            double z, double a) {
-  const int local = (int)(cellkey - R.cell_base);
+__device__ __forceinline__ void store_df3(double4_32a* base, int64_t p, const DF3& v,
+                                          float w, float wl = 0.0f) {
+  float4* r = reinterpret_cast<float4*>(base + p);
+  r[0] = make_float4(v.x.hi, v.y.hi, v.z.hi, w);
+  r[1] = make_float4(v.x.lo, v.y.lo, v.z.lo, wl);
+}
+
+// Mirrors of one sphere (see the file comment): pm[0]/pm[1] are the hi/lo
+// halves of (offset, radius).  `ct` is tilt/ncy and `tilt` the tilt, both
+// double-float, of the box the positions are wrapped in.
+__device__ __forceinline__ void make_mirrors(const Replica& R, df tilt, df ct, int cellkey,
+                                             const DF3& x, df a, const DF3& U,
+                                             const DF3& W, int tag, float4* pm,
+                                             float4& vm, float4& om) {
+  const int local = cellkey - (int)R.cell_base;
   const int cx = local % R.nc[0], cy = (local / R.nc[0]) % R.nc[1],
             cz = local / (R.nc[0] * R.nc[1]);
-  const double sx = cx * R.hcell[0], sy = cy * R.hcell[1], sz = cz * R.hcell[2];
-  double dx = x - (R.L[0] * sx + tilt * sy);
-  double dy = y - R.L[1] * sy;
-  double dz = z - R.L[2] * sz;
-  const double my = rint(dy / R.L[1]);
-  dy -= my * R.L[1];
-  dx -= my * tilt;
-  dx -= rint(dx / R.L[0]) * R.L[0];
-  dz -= rint(dz / R.L[2]) * R.L[2];
-  return make_float4((float)dx, (float)dy, (float)dz, (float)a);
+  // home-cell origin in the lab frame
+  const df ox = df_add(df_mul_f(df{R.cw_hi[0], R.cw_lo[0]}, (float)cx), df_mul_f(ct, (float)cy));
+  const df oy = df_mul_f(df{R.cw_hi[1], R.cw_lo[1]}, (float)cy);
+  const df oz = df_mul_f(df{R.cw_hi[2], R.cw_lo[2]}, (float)cz);
+  df dx = df_sub(x.x, ox), dy = df_sub(x.y, oy), dz = df_sub(x.z, oz);
+  // nearest image of the offset (a sphere wrapped across a face)
+  const df Lx{R.L_hi[0], R.L_lo[0]}, Ly{R.L_hi[1], R.L_lo[1]}, Lz{R.L_hi[2], R.L_lo[2]};
+  const float my = rintf(df_to_f(dy) / R.L_hi[1]);
+  if (my != 0.0f) {
+    dy = df_sub(dy, df_mul_f(Ly, my));
+    dx = df_sub(dx, df_mul_f(tilt, my));
+  }
+  const float mx = rintf(df_to_f(dx) / R.L_hi[0]);
+  if (mx != 0.0f) dx = df_sub(dx, df_mul_f(Lx, mx));
+  const float mz = rintf(df_to_f(dz) / R.L_hi[2]);
+  if (mz != 0.0f) dz = df_sub(dz, df_mul_f(Lz, mz));
+  pm[0] = make_float4(dx.hi, dy.hi, dz.hi, a.hi);
+  pm[1] = make_float4(dx.lo, dy.lo, dz.lo, a.lo);
+  // U - rate (y - Ly/2)
+  const df yrel = df_sub(x.y, df{R.yc_hi, R.yc_lo});
+  const df ux = df_sub(U.x, df_mul(yrel, df{R.rate_hi, R.rate_lo}));
+  vm = make_float4(df_to_f(ux), df_to_f(U.y), df_to_f(U.z), __int_as_float(tag));
+  // home cell coordinates packed 10 bits each (nc <= 1023 per axis)
+  const int pack = cx | (cy << 10) | (cz << 20);
+  om = make_float4(df_to_f(W.x), df_to_f(W.y), df_to_f(W.z), __int_as_float(pack));
 }
 
-__device__ __forceinline__ bool wrap_le_m(double& x, double& y, double& z,
-                                          double& ux, const double* L,
-                                          double tilt, double dUx) {
-  if (!isfinite(x + y + z)) return false;
+__device__ __forceinline__ bool wrap_df(DF3& x, df& ux, const Replica& R, df tilt) {
+  const df Lx{R.L_hi[0], R.L_lo[0]}, Ly{R.L_hi[1], R.L_lo[1]}, Lz{R.L_hi[2], R.L_lo[2]};
+  const df du{R.dux_hi, R.dux_lo};
+  if (!isfinite(x.x.hi + x.y.hi + x.z.hi)) return false;
   int guard = 0;
-  while (y >= L[1] && guard < 64) { y -= L[1]; x -= tilt; ux -= dUx; ++guard; }
-  while (y < 0.0 && guard < 64) { y += L[1]; x += tilt; ux += dUx; ++guard; }
-  while (x >= L[0] && guard < 64) { x -= L[0]; ++guard; }
-  while (x < 0.0 && guard < 64) { x += L[0]; ++guard; }
-  while (z >= L[2] && guard < 64) { z -= L[2]; ++guard; }
-  while (z < 0.0 && guard < 64) { z += L[2]; ++guard; }
+  while (df_ge(x.y, Ly) && guard < 64) { x.y = df_sub(x.y, Ly); x.x = df_sub(x.x, tilt); ux = df_sub(ux, du); ++guard; }
+  while (df_lt0(x.y) && guard < 64) { x.y = df_add(x.y, Ly); x.x = df_add(x.x, tilt); ux = df_add(ux, du); ++guard; }
+  while (df_ge(x.x, Lx) && guard < 64) { x.x = df_sub(x.x, Lx); ++guard; }
+  while (df_lt0(x.x) && guard < 64) { x.x = df_add(x.x, Lx); ++guard; }
+  while (df_ge(x.z, Lz) && guard < 64) { x.z = df_sub(x.z, Lz); ++guard; }
+  while (df_lt0(x.z) && guard < 64) { x.z = df_add(x.z, Lz); ++guard; }
   return guard < 64;
 }
 
-__device__ void integrator_epilogue_m(const Arrays& A, const StepArgs& s,
-                                      unsigned long long cond_handle,
-                                      int use_cond) {
+__device__ __forceinline__ void kick(DF3& v, float4 f, float c) {
+  v.x = df_add_f(v.x, c * f.x);
+  v.y = df_add_f(v.y, c * f.y);
+  v.z = df_add_f(v.z, c * f.z);
+}
+
+// Last-block bookkeeping (strain, k, rebuild decision) as in the FP64 path,
+// plus the double-float fields the next step reads.
+__device__ void epilogue_mixed(const Arrays& A, const StepArgs& s,
+                               unsigned long long cond_handle, int use_cond) {
   Ctl* ctl = A.ctl;
   for (int r = 0; r < A.R; ++r) {
     Replica& R = A.repl[r];
-    const double st = next_strain_m(R);
+    const double st = advance_strain(R.strain, R.rate_dt, R.flip_at, R.flip_by);
+    // a flip moves every home-cell origin by a fraction of Lx: the
+    // cell-relative mirrors need fresh home cells
+    if (st < R.strain && R.rate_dt > 0.0) ctl->need_rebuild = 1;
     R.strain = st;
-    R.tilt = st * R.L[1];
+    R.tilt = R.strain * R.L[1];
+    refresh_strain_fields(R);
   }
   ctl->k = ctl->k + 1;
-  const double vmax = __longlong_as_double((long long)ctl->vmax_bits);
-  ctl->vmax_bits = 0ull;
+  const double vmax = (double)__uint_as_float(ctl->vmax_fbits);
+  ctl->vmax_fbits = 0u;
   ctl->disp_bound = ctl->disp_bound + s.dt * vmax;
   ctl->t_since_build = ctl->t_since_build + s.dt;
   const double D = ctl->disp_bound;
@@ -91,11 +132,10 @@ __device__ void integrator_epilogue_m(const Arrays& A, const StepArgs& s,
   ctl->ticket = 0u;
 }
 
-// Fused close/open half kicks, drift, strain advance, wrap, mirrors (see the
-// FP64 integrator for the step structure).
 __global__ void __launch_bounds__(kBlock)
 k_integrate_mixed(Arrays A, BlockMap bm, StepArgs s, int close, int sample_kin,
-                  unsigned long long cond_handle, int use_cond) {
+                  unsigned long long cond_handle, int use_cond, float dt_hi, float dt_lo,
+                  float hdt) {
   __shared__ double smem[(kBlock / 32) * kKinLen];
   __shared__ bool last;
   const int b = blockIdx.x;
@@ -105,75 +145,101 @@ k_integrate_mixed(Arrays A, BlockMap bm, StepArgs s, int close, int sample_kin,
   Ctl* ctl = A.ctl;
   const int cur = ctl->cur;
   const Replica& RP = A.repl[r];
-  const double L[3] = {RP.L[0], RP.L[1], RP.L[2]};
-  const double rate = RP.rate;
-  const double tilt = next_strain_m(RP) * L[1];
-  const double hdt = s.hdt, dt = s.dt;
-  const int64_t Np = A.Npad;
-  double kin[kKinLen];
+  const df tilt{RP.nt_hi, RP.nt_lo};   // tilt after this step's strain advance
+  const df ct{RP.nct_hi, RP.nct_lo};
+  const df dt{dt_hi, dt_lo};
+  float kin[kKinLen];
 #pragma unroll
-  for (int q = 0; q < kKinLen; ++q) kin[q] = 0.0;
-  double vpec = 0.0;
+  for (int q = 0; q < kKinLen; ++q) kin[q] = 0.0f;
+  float vpec = 0.0f;
   if (active) {
-    double4_32a P = A.pos[cur][p];
-    double4_32a V = A.vel[cur][p];
-    double4_32a W = A.omg[cur][p];
-    double* F = A.frc[cur];
-    double* T = A.trq[cur];
-    const double im = 1.0 / V.w, iI = 1.0 / W.w;
-    const double a0 = hdt * F[p] * im, a1 = hdt * F[Np + p] * im, a2 = hdt * F[2 * Np + p] * im;
-    const double b0 = hdt * T[p] * iI, b1 = hdt * T[Np + p] * iI, b2 = hdt * T[2 * Np + p] * iI;
+    DF3 x, U, W;
+    float a, alo, im, iI;
+    load_df3(A.pos[cur], p, x, a, &alo);
+    load_df3(A.vel[cur], p, U, im);
+    load_df3(A.omg[cur], p, W, iI);
+    float4* F4 = reinterpret_cast<float4*>(A.frc[cur]);
+    float4* T4 = reinterpret_cast<float4*>(A.trq[cur]);
+    const float4 f = F4[p], t = T4[p];
+    const float cm = hdt * im, cI = hdt * iI;
     if (close) {
-      V.x += a0; V.y += a1; V.z += a2;
-      W.x += b0; W.y += b1; W.z += b2;
+      kick(U, f, cm);
+      kick(W, t, cI);
       if (sample_kin) {
-        const double u[3] = {V.x - rate * (P.y - 0.5 * L[1]), V.y, V.z};
-        const double w[3] = {W.x, W.y, W.z + 0.5 * rate};
+        const df yrel = df_sub(x.y, df{RP.yc_hi, RP.yc_lo});
+        const float u[3] = {df_to_f(df_sub(U.x, df_mul(yrel, df{RP.rate_hi, RP.rate_lo}))),
+                            df_to_f(U.y), df_to_f(U.z)};
+        const float w[3] = {df_to_f(W.x), df_to_f(W.y), df_to_f(W.z) + 0.5f * RP.rate_f};
+        const float m = 1.0f / im, I = 1.0f / iI;
 #pragma unroll
         for (int al = 0; al < 3; ++al)
 #pragma unroll
           for (int be = 0; be < 3; ++be) {
-            kin[3 * al + be] = V.w * u[al] * u[be];
-            kin[9 + 3 * al + be] = W.w * w[al] * w[be];
+            kin[3 * al + be] = m * u[al] * u[be];
+            kin[9 + 3 * al + be] = I * w[al] * w[be];
           }
       }
     }
-    V.x += a0; V.y += a1; V.z += a2;
-    W.x += b0; W.y += b1; W.z += b2;
-    P.x += dt * V.x; P.y += dt * V.y; P.z += dt * V.z;
-    if (!wrap_le_m(P.x, P.y, P.z, V.x, L, tilt, rate * L[1]))
+    kick(U, f, cm);
+    kick(W, t, cI);
+    x.x = df_add(x.x, df_mul(U.x, dt));
+    x.y = df_add(x.y, df_mul(U.y, dt));
+    x.z = df_add(x.z, df_mul(U.z, dt));
+    if (!wrap_df(x, U.x, RP, tilt)) atomicOr(&ctl->err, kErrNonFinite);
+    if (!isfinite(U.x.hi + U.y.hi + U.z.hi + W.x.hi + W.y.hi + W.z.hi))
       atomicOr(&ctl->err, kErrNonFinite);
-    if (!isfinite(V.x + V.y + V.z + W.x + W.y + W.z)) atomicOr(&ctl->err, kErrNonFinite);
-    A.pos[cur][p] = P;
-    A.vel[cur][p] = V;
-    A.omg[cur][p] = W;
-    F[p] = 0.0; F[Np + p] = 0.0; F[2 * Np + p] = 0.0;
-    T[p] = 0.0; T[Np + p] = 0.0; T[2 * Np + p] = 0.0;
-    const double ux = V.x - rate * (P.y - 0.5 * L[1]);
-    A.posm[p] = make_posm(RP, tilt, A.cell[p], P.x, P.y, P.z, P.w);
-    A.velm[p] = make_float4((float)ux, (float)V.y, (float)V.z, 0.0f);
-    A.omgm[p] = make_float4((float)W.x, (float)W.y, (float)W.z, 0.0f);
-    vpec = sqrt(ux * ux + V.y * V.y + V.z * V.z);
-    if (!(vpec == vpec)) vpec = 0.0;
+    store_df3(A.pos[cur], p, x, a, alo);
+    store_df3(A.vel[cur], p, U, im);
+    store_df3(A.omg[cur], p, W, iI);
+    F4[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+    T4[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 pm[2], vm, om;
+    make_mirrors(RP, tilt, ct, A.cell[p], x, df{a, alo}, U, W, A.tag[cur][p], pm, vm, om);
+    A.posm[2 * p] = pm[0];
+    A.posm[2 * p + 1] = pm[1];
+    A.velm[p] = vm;
+    A.omgm[p] = om;
+    vpec = sqrtf(vm.x * vm.x + vm.y * vm.y + vm.z * vm.z);
+    if (!(vpec == vpec)) vpec = 0.0f;
   }
-  const double bmax = block_max(vpec, smem);
-  if (threadIdx.x == 0) atomicMax(&ctl->vmax_bits, (unsigned long long)__double_as_longlong(bmax));
-  if (close && sample_kin)
-    block_sum_write<kKinLen>(kin, smem, A.kin_partial + (int64_t)b * kKinLen);
+  // warp max of the peculiar speed in single precision; non-negative floats
+  // order like their bit patterns, so an integer atomicMax is a float max
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) vpec = fmaxf(vpec, __shfl_down_sync(0xffffffffu, vpec, o));
+  if (lane == 0) atomicMax(&ctl->vmax_fbits, __float_as_uint(vpec));
+  if (close && sample_kin) {
+    // single-precision warp and block sums, double across blocks and time
+    float* sk = reinterpret_cast<float*>(smem);
+#pragma unroll
+    for (int q = 0; q < kKinLen; ++q) {
+      float v = kin[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) sk[warp * kKinLen + q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kKinLen) {
+      float sum = 0.0f;
+      for (int w2 = 0; w2 < kBlock / 32; ++w2) sum += sk[w2 * kKinLen + threadIdx.x];
+      A.kin_partial[(int64_t)b * kKinLen + threadIdx.x] = (double)sum;
+    }
+  }
   __threadfence();
   if (threadIdx.x == 0) {
-    const unsigned int t = atomicAdd(&ctl->ticket, 1u);
-    last = (t == (unsigned int)gridDim.x - 1u);
+    const unsigned int tk = atomicAdd(&ctl->ticket, 1u);
+    last = (tk == (unsigned int)gridDim.x - 1u);
   }
   __syncthreads();
   if (last && threadIdx.x == 0) {
     __threadfence();
-    integrator_epilogue_m(A, s, cond_handle, use_cond);
+    epilogue_mixed(A, s, cond_handle, use_cond);
   }
 }
 
+// Closing half kick at the end of a call (double-float).
 __global__ void __launch_bounds__(kBlock)
-k_finalize_mixed(Arrays A, BlockMap bm, StepArgs s, int sample_kin) {
+k_finalize_mixed(Arrays A, BlockMap bm, StepArgs s, int sample_kin, float hdt) {
   __shared__ double smem[(kBlock / 32) * kKinLen];
   const int b = blockIdx.x;
   const int r = bm.rep[b];
@@ -181,293 +247,166 @@ k_finalize_mixed(Arrays A, BlockMap bm, StepArgs s, int sample_kin) {
   const bool active = p < bm.end[b];
   const int cur = A.ctl->cur;
   const Replica& RP = A.repl[r];
-  const double rate = RP.rate, Ly = RP.L[1];
-  const double hdt = s.hdt;
-  const int64_t Np = A.Npad;
-  double kin[kKinLen];
+  float kin[kKinLen];
 #pragma unroll
-  for (int q = 0; q < kKinLen; ++q) kin[q] = 0.0;
+  for (int q = 0; q < kKinLen; ++q) kin[q] = 0.0f;
   if (active) {
-    const double4_32a P = A.pos[cur][p];
-    double4_32a V = A.vel[cur][p];
-    double4_32a W = A.omg[cur][p];
-    const double* F = A.frc[cur];
-    const double* T = A.trq[cur];
-    const double im = 1.0 / V.w, iI = 1.0 / W.w;
-    V.x += hdt * F[p] * im; V.y += hdt * F[Np + p] * im; V.z += hdt * F[2 * Np + p] * im;
-    W.x += hdt * T[p] * iI; W.y += hdt * T[Np + p] * iI; W.z += hdt * T[2 * Np + p] * iI;
-    A.vel[cur][p] = V;
-    A.omg[cur][p] = W;
+    DF3 x, U, W;
+    float a, im, iI;
+    load_df3(A.pos[cur], p, x, a);
+    load_df3(A.vel[cur], p, U, im);
+    load_df3(A.omg[cur], p, W, iI);
+    const float4 f = reinterpret_cast<const float4*>(A.frc[cur])[p];
+    const float4 t = reinterpret_cast<const float4*>(A.trq[cur])[p];
+    kick(U, f, hdt * im);
+    kick(W, t, hdt * iI);
+    store_df3(A.vel[cur], p, U, im);
+    store_df3(A.omg[cur], p, W, iI);
     if (sample_kin) {
-      const double u[3] = {V.x - rate * (P.y - 0.5 * Ly), V.y, V.z};
-      const double w[3] = {W.x, W.y, W.z + 0.5 * rate};
+      const df yrel = df_sub(x.y, df{RP.yc_hi, RP.yc_lo});
+      const float u[3] = {df_to_f(df_sub(U.x, df_mul(yrel, df{RP.rate_hi, RP.rate_lo}))),
+                          df_to_f(U.y), df_to_f(U.z)};
+      const float w[3] = {df_to_f(W.x), df_to_f(W.y), df_to_f(W.z) + 0.5f * RP.rate_f};
+      const float m = 1.0f / im, I = 1.0f / iI;
 #pragma unroll
       for (int al = 0; al < 3; ++al)
 #pragma unroll
         for (int be = 0; be < 3; ++be) {
-          kin[3 * al + be] = V.w * u[al] * u[be];
-          kin[9 + 3 * al + be] = W.w * w[al] * w[be];
+          kin[3 * al + be] = m * u[al] * u[be];
+          kin[9 + 3 * al + be] = I * w[al] * w[be];
         }
     }
   }
-  if (sample_kin) block_sum_write<kKinLen>(kin, smem, A.kin_partial + (int64_t)b * kKinLen);
+  if (sample_kin) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* sk = reinterpret_cast<float*>(smem);
+#pragma unroll
+    for (int q = 0; q < kKinLen; ++q) {
+      float v = kin[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) sk[warp * kKinLen + q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kKinLen) {
+      float sum = 0.0f;
+      for (int w2 = 0; w2 < kBlock / 32; ++w2) sum += sk[w2 * kKinLen + threadIdx.x];
+      A.kin_partial[(int64_t)b * kKinLen + threadIdx.x] = (double)sum;
+    }
+  }
+  (void)s;
 }
 
-// Mirrors of the live copy from scratch (after a rebuild or a state change).
-__global__ void k_mirror(Arrays A, int gated, int use_next) {
+// Mirrors from the state: after a rebuild (gated, new order) or a state change.
+__global__ void k_mirror_mixed(Arrays A, int gated, int use_next) {
   if (gated && *(volatile const int*)&A.ctl->need_rebuild == 0) return;
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= A.N) return;
   const int c = use_next ? (A.ctl->cur ^ 1) : A.ctl->cur;
   const int r = A.rep[c][p];
   const Replica& R = A.repl[r];
-  const double4_32a P = A.pos[c][p];
-  const double4_32a V = A.vel[c][p];
-  const double4_32a W = A.omg[c][p];
-  A.posm[p] = make_posm(R, R.tilt, A.cell[p], P.x, P.y, P.z, P.w);
-  const double ux = V.x - R.rate * (P.y - 0.5 * R.L[1]);
-  A.velm[p] = make_float4((float)ux, (float)V.y, (float)V.z, 0.0f);
-  A.omgm[p] = make_float4((float)W.x, (float)W.y, (float)W.z, 0.0f);
+  DF3 x, U, W;
+  float a, alo, im, iI;
+  load_df3(A.pos[c], p, x, a, &alo);
+  load_df3(A.vel[c], p, U, im);
+  load_df3(A.omg[c], p, W, iI);
+  const df tilt = df_from_d(R.tilt);  // off the per-step path
+  float4 pm[2], vm, om;
+  make_mirrors(R, tilt, df{R.ct_hi, R.ct_lo}, A.cell[p], x, df{a, alo}, U, W, A.tag[c][p],
+               pm, vm, om);
+  A.posm[2 * p] = pm[0];
+  A.posm[2 * p + 1] = pm[1];
+  A.velm[p] = vm;
+  A.omgm[p] = om;
 }
 
-// ---------------------------------------------------------------------------
-// pair kernel, single-precision arithmetic
-// ---------------------------------------------------------------------------
-template <bool NOISE, bool FRIC, bool SAMPLE>
-__global__ void __launch_bounds__(kBlock)
-k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
-  __shared__ double smem[(kBlock / 32) * kPartialLen];
-  const int b = blockIdx.x;
-  const int r = bm.rep[b];
-  const int p = bm.start[b] + threadIdx.x;
-  const bool active = p < bm.end[b];
-  const Ctl* ctl = A.ctl;
-  const int cur = ctl->cur;
-  const long long k = ctl->k;
-  const Replica& RP = A.repl[r];
-  const float rate = (float)RP.rate;
-  const float eta = (float)RP.eta, kn = (float)RP.kn, kt = (float)RP.kt;
-  const double mu = RP.mu, kt_d = RP.kt, kn_d = RP.kn;
-  const float c = (float)RP.noise_c;
-  const float cwx = (float)(RP.L[0] * RP.hcell[0]);
-  const float cwy = (float)(RP.L[1] * RP.hcell[1]);
-  const float cwz = (float)(RP.L[2] * RP.hcell[2]);
-  const float ctilt = (float)(RP.tilt * RP.hcell[1]);
-  const int ncx = RP.nc[0], ncy = RP.nc[1], ncz = RP.nc[2];
-  const int64_t cbase = RP.cell_base;
-  const uint32_t key0 = RP.key0, key1 = RP.key1;
-  const int64_t t0 = RP.p0;
-  const int64_t Np = A.Npad;
-  const float xi_min = (float)s.xi_min, xi_max = (float)s.xi_max;
-  const float tsign = (float)s.torque_sign;
-
-  float vir[kPartialLen];
-#pragma unroll
-  for (int q = 0; q < kPartialLen; ++q) vir[q] = 0.0f;
-
-  if (active) {
-    const float4 P = A.posm[p];
-    const float4 VP = A.velm[p];
-    const float4 WP = A.omgm[p];
-    const int tp = A.tag[cur][p];
-    const int lp = A.cell[p] - (int)cbase;
-    const int pcx = lp % ncx, pcy = (lp / ncx) % ncy, pcz = lp / (ncx * ncy);
-    const float ap = P.w;
-    float F[3] = {0.f, 0.f, 0.f}, T[3] = {0.f, 0.f, 0.f};
-    if (s.onebody) {
-      const float pi = 3.14159265358979f;
-      const float gt = 6.0f * pi * eta * ap;
-      const float gr = 8.0f * pi * eta * ap * ap * ap;
-      float g[6] = {0, 0, 0, 0, 0, 0};
-      if (NOISE) gauss6_f32(key0, key1, k, (uint32_t)(tp - t0), (uint32_t)(tp - t0), g);
-      const float ct = c * sqrtf(gt), cr = c * sqrtf(gr);
-      // U_inf - U = -u (peculiar velocity); Omega_inf - Omega
-      F[0] = -gt * VP.x + (NOISE ? ct * g[0] : 0.f);
-      F[1] = -gt * VP.y + (NOISE ? ct * g[1] : 0.f);
-      F[2] = -gt * VP.z + (NOISE ? ct * g[2] : 0.f);
-      T[0] = -gr * WP.x + (NOISE ? cr * g[3] : 0.f);
-      T[1] = -gr * WP.y + (NOISE ? cr * g[4] : 0.f);
-      T[2] = gr * (-0.5f * rate - WP.z) + (NOISE ? cr * g[5] : 0.f);
-    }
-    const int nn = A.nnb[cur][p];
-    const int* __restrict__ row = A.nbr[cur] + p;
-    unsigned long long cm_old = 0ull, cm_new = 0ull;
-    if (FRIC) cm_old = A.cmsk[cur][p];
-    double* __restrict__ hist = FRIC ? A.hist[cur] : nullptr;
-    const int64_t hstride = (int64_t)A.kmax * Np;
-
-    for (int sl = 0; sl < nn; ++sl) {
-      const int q = __ldg(row + (int64_t)sl * Np);
-      const float4 Q = __ldg(A.posm + q);
-      const int lq = __ldg(A.cell + q) - (int)cbase;
-      int dcx = lq % ncx - pcx, dcy = (lq / ncx) % ncy - pcy, dcz = lq / (ncx * ncy) - pcz;
-      dcx = dcx > 1 ? dcx - ncx : (dcx < -1 ? dcx + ncx : dcx);
-      dcy = dcy > 1 ? dcy - ncy : (dcy < -1 ? dcy + ncy : dcy);
-      dcz = dcz > 1 ? dcz - ncz : (dcz < -1 ? dcz + ncz : dcz);
-      float rpq[3];
-      rpq[0] = (Q.x - P.x) + (cwx * (float)dcx + ctilt * (float)dcy);
-      rpq[1] = (Q.y - P.y) + cwy * (float)dcy;
-      rpq[2] = (Q.z - P.z) + cwz * (float)dcz;
-      const float d2 = rpq[0] * rpq[0] + rpq[1] * rpq[1] + rpq[2] * rpq[2];
-      const float S = ap + Q.w;
-      const float d = sqrtf(d2);
-      const float h = d - S;
-      const float xi = 2.0f * h / S;
-      if (xi > xi_max) continue;
-      const float4 VQ = __ldg(A.velm + q);
-      const float4 WQ = __ldg(A.omgm + q);
-      const int tq = __ldg(A.tag[cur] + q);
-      const bool p_is_i = tp < tq;
-      const float sg = p_is_i ? 1.0f : -1.0f;
-      const float rr[3] = {sg * rpq[0], sg * rpq[1], sg * rpq[2]};
-      const float ai = p_is_i ? ap : Q.w, aj = p_is_i ? Q.w : ap;
-      const float Ui[3] = {p_is_i ? VP.x : VQ.x, p_is_i ? VP.y : VQ.y, p_is_i ? VP.z : VQ.z};
-      const float Uj[3] = {p_is_i ? VQ.x : VP.x, p_is_i ? VQ.y : VP.y, p_is_i ? VQ.z : VP.z};
-      const float Wi[3] = {p_is_i ? WP.x : WQ.x, p_is_i ? WP.y : WQ.y, p_is_i ? WP.z : WQ.z};
-      const float Wj[3] = {p_is_i ? WQ.x : WP.x, p_is_i ? WQ.y : WP.y, p_is_i ? WQ.z : WP.z};
-      const float id = 1.0f / d;
-      const float n[3] = {rr[0] * id, rr[1] * id, rr[2] * id};
-      const float dU[3] = {Uj[0] - Ui[0] + rate * rr[1], Uj[1] - Ui[1], Uj[2] - Ui[2]};
-      PairOut<float> o;
-      if (s.lubrication) {
-        const float xi_e = xi < xi_min ? xi_min : xi;
-        const float lg = -__logf(xi_e);
-        const Res8<float> R = resistances<float>(eta, ai, aj, xi_e, lg);
-        float g[6] = {0, 0, 0, 0, 0, 0};
-        const int li = (int)((p_is_i ? tp : tq) - t0);
-        const int lj = (int)((p_is_i ? tq : tp) - t0);
-        if (NOISE) gauss6_f32(key0, key1, k, (uint32_t)li, (uint32_t)lj, g);
-        lub_brownian<float, NOISE>(R, n, dU, Wi, Wj, g, g + 3, c, tsign, o);
-      } else {
-#pragma unroll
-        for (int q3 = 0; q3 < 3; ++q3) o.FL[q3] = o.FB[q3] = o.Ti[q3] = o.Tj[q3] = 0.f;
-      }
-      float FC[3] = {0.f, 0.f, 0.f}, TCi[3] = {0.f, 0.f, 0.f}, TCj[3] = {0.f, 0.f, 0.f};
-      if (h < 0.0f && s.contact) {
-        const float delta = -h;
-        float Ft[3] = {0.f, 0.f, 0.f};
-        if (FRIC && mu > 0.0) {
-          double xt[3] = {0.0, 0.0, 0.0};
-          const int64_t hi = (int64_t)sl * Np + p;
-          if ((cm_old >> sl) & 1ull) {
-            xt[0] = hist[hi]; xt[1] = hist[hi + hstride]; xt[2] = hist[hi + 2 * hstride];
-          }
-          if (s.advance) {
-            const float ww[3] = {ai * Wi[0] + aj * Wj[0], ai * Wi[1] + aj * Wj[1],
-                                 ai * Wi[2] + aj * Wj[2]};
-            float wxn[3];
-            cross3(ww, n, wxn);
-            const double v[3] = {(double)(dU[0] - wxn[0]), (double)(dU[1] - wxn[1]),
-                                 (double)(dU[2] - wxn[2])};
-            const double nd[3] = {(double)n[0], (double)n[1], (double)n[2]};
-            history_update(xt, nd, v, s.dt, kt_d, mu * kn_d * (double)delta);
-          }
-          hist[hi] = xt[0]; hist[hi + hstride] = xt[1]; hist[hi + 2 * hstride] = xt[2];
-          cm_new |= 1ull << sl;
-          Ft[0] = kt * (float)xt[0]; Ft[1] = kt * (float)xt[1]; Ft[2] = kt * (float)xt[2];
-        }
-#pragma unroll
-        for (int q3 = 0; q3 < 3; ++q3) FC[q3] = -kn * delta * n[q3] + Ft[q3];
-        float nxF[3];
-        cross3(n, Ft, nxF);
-#pragma unroll
-        for (int q3 = 0; q3 < 3; ++q3) {
-          TCi[q3] = ai * nxF[q3];
-          TCj[q3] = aj * nxF[q3];
-        }
-      }
-      float Fi[3], Ti_[3], Tj_[3];
-#pragma unroll
-      for (int q3 = 0; q3 < 3; ++q3) {
-        Fi[q3] = FC[q3] + o.FL[q3] + o.FB[q3];
-        Ti_[q3] = TCi[q3] + o.Ti[q3];
-        Tj_[q3] = TCj[q3] + o.Tj[q3];
-      }
-      const int64_t qo = q;
-#pragma unroll
-      for (int q3 = 0; q3 < 3; ++q3) {
-        F[q3] += sg * Fi[q3];
-        T[q3] += p_is_i ? Ti_[q3] : Tj_[q3];
-        atomicAdd(A.frc[cur] + q3 * Np + qo, (double)(-sg * Fi[q3]));
-        atomicAdd(A.trq[cur] + q3 * Np + qo, (double)(p_is_i ? Tj_[q3] : Ti_[q3]));
-      }
-      if (SAMPLE) {
-#pragma unroll
-        for (int al = 0; al < 3; ++al)
-#pragma unroll
-          for (int be = 0; be < 3; ++be) {
-            vir[3 * al + be] += FC[al] * rr[be];
-            vir[9 + 3 * al + be] += o.FL[al] * rr[be];
-            vir[18 + 3 * al + be] += o.FB[al] * rr[be];
-          }
-      }
-    }
-    if (FRIC) A.cmsk[cur][p] = cm_new;
-#pragma unroll
-    for (int q3 = 0; q3 < 3; ++q3) {
-      atomicAdd(A.frc[cur] + q3 * Np + p, (double)F[q3]);
-      atomicAdd(A.trq[cur] + q3 * Np + p, (double)T[q3]);
-    }
+// Host state (tag order, doubles) into the live copy in double-float form.
+__global__ void k_load_state_mixed(Arrays A, const double* __restrict__ x,
+                                   const double* __restrict__ U,
+                                   const double* __restrict__ W,
+                                   const double* __restrict__ radius,
+                                   const double* __restrict__ mass,
+                                   const double* __restrict__ inertia,
+                                   const int* __restrict__ rep_of) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= A.N) return;
+  const int cur = A.ctl->cur;
+  const int r = rep_of[p];
+  const Replica& R = A.repl[r];
+  double px = x[3 * p], py = x[3 * p + 1], pz = x[3 * p + 2];
+  double ux = U ? U[3 * p] : 0.0, uy = U ? U[3 * p + 1] : 0.0, uz = U ? U[3 * p + 2] : 0.0;
+  const double wx = W ? W[3 * p] : 0.0, wy = W ? W[3 * p + 1] : 0.0, wz = W ? W[3 * p + 2] : 0.0;
+  const double dUx = R.rate * R.L[1];
+  if (isfinite(px + py + pz)) {
+    int guard = 0;
+    while (py >= R.L[1] && guard < 1024) { py -= R.L[1]; px -= R.tilt; ux -= dUx; ++guard; }
+    while (py < 0.0 && guard < 1024) { py += R.L[1]; px += R.tilt; ux += dUx; ++guard; }
+    while (px >= R.L[0] && guard < 1024) { px -= R.L[0]; ++guard; }
+    while (px < 0.0 && guard < 1024) { px += R.L[0]; ++guard; }
+    while (pz >= R.L[2] && guard < 1024) { pz -= R.L[2]; ++guard; }
+    while (pz < 0.0 && guard < 1024) { pz += R.L[2]; ++guard; }
+    if (guard >= 1024) atomicOr(&A.ctl->err, kErrWrap);
+  } else {
+    atomicOr(&A.ctl->err, kErrNonFinite);
   }
-  if (SAMPLE) {
-    // per-thread single-precision partials, warp sums in single precision,
-    // block and global accumulation in double
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int cc = 0; cc < kPartialLen; ++cc) {
-      float x = vir[cc];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-      if (lane == 0) smem[warp * kPartialLen + cc] = (double)x;
-    }
-    __syncthreads();
-    if (threadIdx.x < kPartialLen) {
-      double sum = 0.0;
-      for (int w = 0; w < kBlock / 32; ++w) sum += smem[w * kPartialLen + threadIdx.x];
-      A.pair_partial[(int64_t)b * kPartialLen + threadIdx.x] = sum;
-    }
-  }
+  DF3 X{df_from_d(px), df_from_d(py), df_from_d(pz)};
+  DF3 V{df_from_d(ux), df_from_d(uy), df_from_d(uz)};
+  DF3 Om{df_from_d(wx), df_from_d(wy), df_from_d(wz)};
+  const df arad = df_from_d(radius[p]);
+  store_df3(A.pos[cur], p, X, arad.hi, arad.lo);
+  store_df3(A.vel[cur], p, V, (float)(1.0 / mass[p]));
+  store_df3(A.omg[cur], p, Om, (float)(1.0 / inertia[p]));
+  reinterpret_cast<float4*>(A.frc[cur])[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+  reinterpret_cast<float4*>(A.trq[cur])[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+  A.tag[cur][p] = (int)p;
+  A.rep[cur][p] = r;
+  A.slot_of_tag[p] = (int)p;
+  A.nnb[cur][p] = 0;
+  A.cmsk[cur][p] = 0ull;
 }
 
-template <bool NOISE, bool FRIC>
-static void launch_pm(const Arrays& A, const BlockMap& bm, const StepArgs& s,
-                      cudaStream_t st) {
-  if (s.sample)
-    k_pair_mixed<NOISE, FRIC, true><<<bm.nblocks, kBlock, 0, st>>>(A, bm, s);
-  else
-    k_pair_mixed<NOISE, FRIC, false><<<bm.nblocks, kBlock, 0, st>>>(A, bm, s);
+__global__ void k_zero_forces_mixed(Arrays A) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= A.N) return;
+  const int cur = A.ctl->cur;
+  reinterpret_cast<float4*>(A.frc[cur])[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+  reinterpret_cast<float4*>(A.trq[cur])[p] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-void launch_pair_mixed(const Arrays& A, const BlockMap& bm, const StepArgs& s,
-                       int tpp, cudaStream_t st) {
-  (void)tpp;
-  const bool noise = s.noise != 0, fric = s.friction != 0;
-  if (noise && fric) launch_pm<true, true>(A, bm, s, st);
-  else if (noise) launch_pm<true, false>(A, bm, s, st);
-  else if (fric) launch_pm<false, true>(A, bm, s, st);
-  else launch_pm<false, false>(A, bm, s, st);
+static inline unsigned grid_of(int64_t n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+void launch_integrate_mixed(const Arrays& A, const BlockMap& bm, const StepArgs& s,
+                            int close, int sample_kin, cudaStream_t st,
+                            unsigned long long cond_handle, int use_cond) {
+  float dth, dtl;
+  split_df(s.dt, dth, dtl);
+  k_integrate_mixed<<<bm.nblocks, kBlock, 0, st>>>(A, bm, s, close, sample_kin, cond_handle,
+                                                   use_cond, dth, dtl, (float)s.hdt);
 }
 
-void launch_integrate_mixed(const Arrays& A, const BlockMap& bm,
-                            const StepArgs& s, int close, int sample_kin,
-                            cudaStream_t st, unsigned long long cond_handle,
-                            int use_cond) {
-  k_integrate_mixed<<<bm.nblocks, kBlock, 0, st>>>(A, bm, s, close, sample_kin,
-                                                   cond_handle, use_cond);
-}
-
-void launch_finalize_mixed(const Arrays& A, const BlockMap& bm,
-                           const StepArgs& s, int sample_kin, cudaStream_t st) {
-  k_finalize_mixed<<<bm.nblocks, kBlock, 0, st>>>(A, bm, s, sample_kin);
+void launch_finalize_mixed(const Arrays& A, const BlockMap& bm, const StepArgs& s,
+                           int sample_kin, cudaStream_t st) {
+  k_finalize_mixed<<<bm.nblocks, kBlock, 0, st>>>(A, bm, s, sample_kin, (float)s.hdt);
 }
 
 void launch_mirror(const Arrays& A, const BlockMap& bm, cudaStream_t st) {
   (void)bm;
-  k_mirror<<<(unsigned)((A.N + kBlock - 1) / kBlock), kBlock, 0, st>>>(A, 0, 0);
+  k_mirror_mixed<<<grid_of(A.N), kBlock, 0, st>>>(A, 0, 0);
 }
 
 void launch_mirror_gated_next(const Arrays& A, cudaStream_t st) {
-  k_mirror<<<(unsigned)((A.N + kBlock - 1) / kBlock), kBlock, 0, st>>>(A, 1, 1);
+  k_mirror_mixed<<<grid_of(A.N), kBlock, 0, st>>>(A, 1, 1);
+}
+
+void launch_load_state_mixed(const Arrays& A, const double* x, const double* U,
+                             const double* W, const double* radius, const double* mass,
+                             const double* inertia, const int* rep_of, cudaStream_t st) {
+  k_load_state_mixed<<<grid_of(A.N), kBlock, 0, st>>>(A, x, U, W, radius, mass, inertia,
+                                                      rep_of);
+}
+
+void launch_zero_forces_mixed(const Arrays& A, cudaStream_t st) {
+  k_zero_forces_mixed<<<grid_of(A.N), kBlock, 0, st>>>(A);
 }
 
 }  // namespace susp

@@ -62,7 +62,7 @@ __global__ void k_cellkey(Arrays A) {
   if (p >= A.N) return;
   const int r = A.rep[cur][p];
   const Replica& R = A.repl[r];
-  const double4_32a P = A.pos[cur][p];
+  const double4_32a P = read_rec_d(A.pos[cur], A.mixed, p);
   const int key = (int)(R.cell_base + cell_index(R, P.x, P.y, P.z, nullptr));
   A.key[p] = key;
   atomicAdd(&A.cell_count[key], 1);
@@ -198,10 +198,15 @@ __global__ void k_permute(Arrays A) {
   A.pos[nxt][p] = A.pos[cur][o];
   A.vel[nxt][p] = A.vel[cur][o];
   A.omg[nxt][p] = A.omg[cur][o];
+  if (A.mixed) {
+    reinterpret_cast<float4*>(A.frc[nxt])[p] = reinterpret_cast<const float4*>(A.frc[cur])[o];
+    reinterpret_cast<float4*>(A.trq[nxt])[p] = reinterpret_cast<const float4*>(A.trq[cur])[o];
+  } else {
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    A.frc[nxt][q * Np + p] = A.frc[cur][q * Np + o];
-    A.trq[nxt][q * Np + p] = A.trq[cur][q * Np + o];
+    for (int q = 0; q < 3; ++q) {
+      A.frc[nxt][q * Np + p] = A.frc[cur][q * Np + o];
+      A.trq[nxt][q * Np + p] = A.trq[cur][q * Np + o];
+    }
   }
   const int t = A.tag[cur][o];
   A.tag[nxt][p] = t;
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Arrays A, StepArgs s, dou
   const Replica& R = A.repl[r];
   const double L[3] = {R.L[0], R.L[1], R.L[2]};
   const double tilt = R.tilt;
-  const double4_32a P = A.pos[nxt][p];
+  const double4_32a P = read_rec_d(A.pos[nxt], A.mixed, p);
   const int local = (int)(A.cell[p] - R.cell_base);
   const int ncx = R.nc[0], ncy = R.nc[1], ncz = R.nc[2];
   const int cx = local % ncx, cy = (local / ncx) % ncy, cz = local / (ncx * ncy);
@@ -237,7 +242,7 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Arrays A, StepArgs s, dou
         const int q0 = A.cell_start[key], q1 = A.cell_start[key + 1];
         for (int q = q0; q < q1; ++q) {
           if (q <= p) continue;
-          const double4_32a Q = A.pos[nxt][q];
+          const double4_32a Q = read_rec_d(A.pos[nxt], A.mixed, q);
           double rr[3], sy;
           min_image_f64(Q.x - P.x, Q.y - P.y, Q.z - P.z, L, tilt, rr, &sy);
           const double d2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
@@ -271,13 +276,13 @@ __global__ void __launch_bounds__(kBlock) k_remap_history(Arrays A) {
   const int r = A.rep[nxt][p];
   const Replica& R = A.repl[r];
   const double L[3] = {R.L[0], R.L[1], R.L[2]};
-  const double4_32a P = A.pos[nxt][p];
+  const double4_32a P = read_rec_d(A.pos[nxt], A.mixed, p);
   const int nn = A.nnb[nxt][p];
   const int op = A.perm[p];
   unsigned long long cm = 0ull;
   for (int sl = 0; sl < nn; ++sl) {
     const int q = A.nbr[nxt][(int64_t)sl * Np + p];
-    const double4_32a Q = A.pos[nxt][q];
+    const double4_32a Q = read_rec_d(A.pos[nxt], A.mixed, q);
     double rr[3], sy;
     min_image_f64(Q.x - P.x, Q.y - P.y, Q.z - P.z, L, R.tilt, rr, &sy);
     const double d2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];

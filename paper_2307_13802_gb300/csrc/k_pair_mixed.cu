@@ -1,0 +1,402 @@
+// k_pair_mixed.cu -- per-timestep pair force evaluation, mixed precision.
+//
+// The same physics as the FP64 kernel (Sec. II.A-II.C: regularised
+// lubrication, pair Brownian force and torques, contact with Coulomb-capped
+// tangential history, one-body drag and noise, pair virials) in single
+// precision on the mirrors written by the integrator, with no FP64-pipe
+// instruction on the per-pair path:
+//   - Work mapping: each warp owns 32 consecutive spheres of the sorted
+//     order and flattens their half-list rows into one work list (a warp
+//     prefix sum of the row lengths); lane l takes items l, l+32, ...  Rows
+//     of uneven length therefore cost no idle lanes.
+//   - Geometry: r = (posm_q - posm_p) + H(t) dc / nc with the home-cell
+//     difference dc in {-1, 0, 1}^3 unpacked from the mirrors; pairs beyond
+//     the lubrication cutoff are rejected on |r|^2 before any square root.
+//   - Accumulation: the owner's share goes to shared-memory float
+//     accumulators (one vector reduction per sphere at the end), the
+//     partner's share straight to its float4 accumulator with one
+//     red.global.add.v4.f32 for the force and one for the torque.
+//   - Tangential history: double-float (hi, lo) per component, updated with
+//     error-free FP32 transformations (dfloat.cuh), so it accumulates with a
+//     48-bit significand.
+//   - Stresses: per-lane single-precision virials, warp sums in single
+//     precision, block, global and time sums in double.
+#include <cuda_runtime.h>
+
+#include "device_common.cuh"
+#include "dfloat.cuh"
+#include "philox.cuh"
+#include "susp_internal.h"
+
+namespace susp {
+
+// Scalar resistances of Eqs. 9-12 and 15-18 in a reciprocal form
+// (beta = a_j/a_i, r = 1/(1+beta), 1/(1+1/beta) = beta r):
+//   XA11 = 6 pi eta a_i r^3 (2 beta^2 / xi + beta (1 + 7 beta + beta^2)/5 L)
+//   YA11 = 6 pi eta a_i r^3 (4 beta (2 + beta + 2 beta^2)/15) L
+//   YB11 = -4 pi eta a_i^2 r^2 (beta (4 + beta)/5) L
+//   YB21 = -4 pi eta a_j^2 r^2 ((4 beta + 1)/5) L
+//   YC11 = 8 pi eta a_i^3 r (2 beta/5) L,   YC12 = 8 pi eta a_i^3 r (beta^2/10) L
+//   YC22 = 8 pi eta a_j^3 r (2/5) L,        YC21 = 8 pi eta a_j^3 r (1/(10 beta)) L
+// with L = ln(1/xi_e).
+__device__ __forceinline__ Res8<float> resistances_f(float eta, float ai, float aj,
+                                                     float ixi, float L) {
+  const float pi = 3.14159265358979f;
+  const float iai = 1.0f / ai;
+  const float beta = aj * iai;
+  const float r = 1.0f / (1.0f + beta);
+  const float r2 = r * r, r3 = r2 * r;
+  const float b2 = beta * beta;
+  const float ta = 6.0f * pi * eta * ai * r3;
+  Res8<float> R;
+  R.XA11 = ta * (2.0f * b2 * ixi + 0.2f * beta * (1.0f + 7.0f * beta + b2) * L);
+  R.YA11 = ta * (4.0f / 15.0f) * beta * (2.0f + beta + 2.0f * b2) * L;
+  const float tb = -4.0f * pi * eta * r2 * 0.2f * L;
+  R.YB11 = tb * ai * ai * beta * (4.0f + beta);
+  R.YB21 = tb * aj * aj * (4.0f * beta + 1.0f);
+  const float tc = 8.0f * pi * eta * r * L;
+  const float ai3 = ai * ai * ai, aj3 = aj * aj * aj;
+  R.YC11 = tc * ai3 * 0.4f * beta;
+  R.YC12 = tc * ai3 * 0.1f * b2;
+  R.YC22 = tc * aj3 * 0.4f;
+  R.YC21 = tc * aj3 * 0.1f / beta;
+  return R;
+}
+
+// Tangential history update in double-float (reading of Sec. II.A): rotate
+// into the current tangent plane keeping the length, add v_t dt, cap at
+// mu kn delta / kt.  xh/xl: hi/lo parts; returns the updated value.
+__device__ __forceinline__ void history_update_df(float* xh, float* xl, const float* n,
+                                                  const float* v, float dt, float kt,
+                                                  float fmax) {
+  df x0{xh[0], xl[0]}, x1{xh[1], xl[1]}, x2{xh[2], xl[2]};
+  const float len0sq = xh[0] * xh[0] + xh[1] * xh[1] + xh[2] * xh[2];
+  if (len0sq > 0.0f) {
+    const float sn = n[0] * xh[0] + n[1] * xh[1] + n[2] * xh[2] +
+                     (n[0] * xl[0] + n[1] * xl[1] + n[2] * xl[2]);
+    const float q = sn * sn / len0sq;
+    if (q < 1.0f) {
+      x0 = df_add_f(x0, -n[0] * sn);
+      x1 = df_add_f(x1, -n[1] * sn);
+      x2 = df_add_f(x2, -n[2] * sn);
+      // restore the length: factor 1/sqrt(1 - q) = 1 + eps
+      const float eps = q < 1e-3f ? q * (0.5f + 0.375f * q) : rsqrtf(1.0f - q) - 1.0f;
+      x0 = df_add_f(x0, x0.hi * eps);
+      x1 = df_add_f(x1, x1.hi * eps);
+      x2 = df_add_f(x2, x2.hi * eps);
+    } else {
+      x0 = x1 = x2 = df{0.f, 0.f};
+    }
+  }
+  const float nv = n[0] * v[0] + n[1] * v[1] + n[2] * v[2];
+  x0 = df_add_f(x0, (v[0] - n[0] * nv) * dt);
+  x1 = df_add_f(x1, (v[1] - n[1] * nv) * dt);
+  x2 = df_add_f(x2, (v[2] - n[2] * nv) * dt);
+  const float ft = kt * sqrtf(x0.hi * x0.hi + x1.hi * x1.hi + x2.hi * x2.hi);
+  if (ft > fmax) {
+    const float sc = fmax / ft;
+    x0 = df{x0.hi * sc, x0.lo * sc};
+    x1 = df{x1.hi * sc, x1.lo * sc};
+    x2 = df{x2.hi * sc, x2.lo * sc};
+  }
+  xh[0] = x0.hi; xh[1] = x1.hi; xh[2] = x2.hi;
+  xl[0] = x0.lo; xl[1] = x1.lo; xl[2] = x2.lo;
+}
+
+__device__ __forceinline__ void unpack_cell(int v, int& cx, int& cy, int& cz) {
+  cx = v & 1023;
+  cy = (v >> 10) & 1023;
+  cz = (v >> 20) & 1023;
+}
+
+__device__ __forceinline__ int wrap_dc(int d, int n) {
+  return d > 1 ? d - n : (d < -1 ? d + n : d);
+}
+
+template <bool NOISE, bool FRIC, bool SAMPLE>
+__global__ void __launch_bounds__(kBlock, 2)
+k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
+  __shared__ float4 sF[kBlock];
+  __shared__ float4 sT[kBlock];
+  __shared__ unsigned long long sM[kBlock];
+  __shared__ float sW[(kBlock / 32) * kPartialLen];
+  __shared__ int sArrive;
+  if (threadIdx.x == 0) sArrive = 0;
+  __syncthreads();
+  const int b = blockIdx.x;
+  const int r = bm.rep[b];
+  const int pb = bm.start[b], pe = bm.end[b];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int p = pb + tid;
+  const bool active = p < pe;
+  const Ctl* ctl = A.ctl;
+  const int cur = ctl->cur;
+  const long long k = ctl->k;
+  const Replica& RP = A.repl[r];
+  const float rate = RP.rate_f, eta = RP.eta_f, kn = RP.kn_f, kt = RP.kt_f, mu = RP.mu_f;
+  const float c = RP.noise_cf;
+  const float cwx = RP.cwf[0], cwy = RP.cwf[1], cwz = RP.cwf[2], ctilt = RP.ctilt_f;
+  const df cw0{RP.cw_hi[0], RP.cw_lo[0]}, cw1{RP.cw_hi[1], RP.cw_lo[1]},
+      cw2{RP.cw_hi[2], RP.cw_lo[2]}, ct_df{RP.ct_hi, RP.ct_lo};
+  const int ncx = RP.nc[0], ncy = RP.nc[1], ncz = RP.nc[2];
+  const uint32_t key0 = RP.key0, key1 = RP.key1;
+  const int t0 = (int)RP.p0;
+  const int64_t Np = A.Npad;
+  const int64_t hs = (int64_t)A.kmax * Np;
+  const float xi_min = s.xi_min_f, xi_max = s.xi_max_f;
+  const float rc_fac = 1.0f + 0.5f * xi_max;
+  const float tsign = s.tsign_f;
+  const float dtf = s.dt_f;
+  const float pi = 3.14159265358979f;
+  float4* __restrict__ F4 = reinterpret_cast<float4*>(A.frc[cur]);
+  float4* __restrict__ T4 = reinterpret_cast<float4*>(A.trq[cur]);
+  const float4* __restrict__ PM = A.posm;
+  const float4* __restrict__ VM = A.velm;
+  const float4* __restrict__ OM = A.omgm;
+  const int* __restrict__ nbr = A.nbr[cur];
+  float2* __restrict__ hist = reinterpret_cast<float2*>(A.hist[cur]);
+
+  // ---- own sphere: one-body drag and noise (Eqs. 5-6, 20-21) -------------
+  int nn = 0;
+  unsigned long long cm_own = 0ull;
+  {
+    float4 f = make_float4(0.f, 0.f, 0.f, 0.f), t = f;
+    if (active) {
+      nn = A.nnb[cur][p];
+      if (FRIC) cm_own = A.cmsk[cur][p];
+      if (s.onebody) {
+        const float4 P = PM[2 * p], V = VM[p], W = OM[p];
+        const float a = P.w;
+        const float gt = 6.0f * pi * eta * a;
+        const float gr = 8.0f * pi * eta * a * a * a;
+        f = make_float4(-gt * V.x, -gt * V.y, -gt * V.z, 0.f);
+        t = make_float4(-gr * W.x, -gr * W.y, gr * (-0.5f * rate - W.z), 0.f);
+        if (NOISE) {
+          float g[6];
+          const uint32_t lt = (uint32_t)(__float_as_int(V.w) - t0);
+          gauss6_f32(key0, key1, k, lt, lt, g);
+          const float ct = c * sqrtf(gt), cr = c * sqrtf(gr);
+          f.x += ct * g[0]; f.y += ct * g[1]; f.z += ct * g[2];
+          t.x += cr * g[3]; t.y += cr * g[4]; t.z += cr * g[5];
+        }
+      }
+    }
+    sF[tid] = f;
+    sT[tid] = t;
+    sM[tid] = 0ull;
+  }
+  // ---- flatten the warp's rows ---------------------------------------------
+  int incl = nn;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  const int excl = incl - nn;
+  __syncwarp();
+
+  float vir[SAMPLE ? kPartialLen : 1];
+#pragma unroll
+  for (int q = 0; q < (SAMPLE ? kPartialLen : 1); ++q) vir[q] = 0.0f;
+
+  for (int base = 0; base < total; base += 32) {
+    const int t = base + lane;
+    // owner lane: first lane whose inclusive row end exceeds t
+    int o = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int v = __shfl_sync(0xffffffffu, incl, o + step - 1);
+      if (v <= t) o += step;
+    }
+    const int oexcl = __shfl_sync(0xffffffffu, excl, o);
+    const unsigned long long ocm = FRIC ? __shfl_sync(0xffffffffu, cm_own, o) : 0ull;
+    if (t >= total) continue;
+    const int sl = t - oexcl;
+    const int po = pb + warp * 32 + o;
+    const int q = __ldg(nbr + (int64_t)sl * Np + po);
+    const float4 P = __ldg(PM + 2 * po), Q = __ldg(PM + 2 * q);
+    const float4 WPo = __ldg(OM + po), WQ = __ldg(OM + q);
+    int pcx, pcy, pcz, qcx, qcy, qcz;
+    unpack_cell(__float_as_int(WPo.w), pcx, pcy, pcz);
+    unpack_cell(__float_as_int(WQ.w), qcx, qcy, qcz);
+    const int dcx = wrap_dc(qcx - pcx, ncx), dcy = wrap_dc(qcy - pcy, ncy),
+              dcz = wrap_dc(qcz - pcz, ncz);
+    float rpq[3];
+    rpq[0] = (Q.x - P.x) + (cwx * (float)dcx + ctilt * (float)dcy);
+    rpq[1] = (Q.y - P.y) + cwy * (float)dcy;
+    rpq[2] = (Q.z - P.z) + cwz * (float)dcz;
+    const float d2f = rpq[0] * rpq[0] + rpq[1] * rpq[1] + rpq[2] * rpq[2];
+    const float rc = (P.w + Q.w) * rc_fac;
+    // beyond the lubrication cutoff (with a margin for single-precision
+    // rounding; the exact test follows): no force, no contact
+    if (d2f > rc * rc * 1.00001f) continue;
+    // separation and gap in double-float: h = (d^2 - S^2) / (d + S)
+    const float4 Pl = __ldg(PM + 2 * po + 1), Ql = __ldg(PM + 2 * q + 1);
+    const df rx = df_add(df_diff(Q.x, Ql.x, P.x, Pl.x),
+                         df_add(df_mul_f(cw0, (float)dcx), df_mul_f(ct_df, (float)dcy)));
+    const df ry = df_add(df_diff(Q.y, Ql.y, P.y, Pl.y), df_mul_f(cw1, (float)dcy));
+    const df rz = df_add(df_diff(Q.z, Ql.z, P.z, Pl.z), df_mul_f(cw2, (float)dcz));
+    const df dd = df_add(df_add(df_mul(rx, rx), df_mul(ry, ry)), df_mul(rz, rz));
+    const df Sd = df_add(df{P.w, Pl.w}, df{Q.w, Ql.w});
+    const float S = Sd.hi;
+    const float d = sqrtf(dd.hi);
+    const float h = df_to_f(df_sub(dd, df_mul(Sd, Sd))) / (d + S);
+    const float xi = 2.0f * h / S;
+    if (xi > xi_max) continue;
+    rpq[0] = df_to_f(rx); rpq[1] = df_to_f(ry); rpq[2] = df_to_f(rz);
+    const float4 VPo = __ldg(VM + po), VQ = __ldg(VM + q);
+    const int tp = __float_as_int(VPo.w), tq = __float_as_int(VQ.w);
+    const bool p_is_i = tp < tq;
+    const float sg = p_is_i ? 1.0f : -1.0f;
+    const float id = 1.0f / d;
+    const float rr[3] = {sg * rpq[0], sg * rpq[1], sg * rpq[2]};
+    const float n[3] = {rr[0] * id, rr[1] * id, rr[2] * id};
+    const float ai = p_is_i ? P.w : Q.w, aj = p_is_i ? Q.w : P.w;
+    const float4 Vi = p_is_i ? VPo : VQ, Vj = p_is_i ? VQ : VPo;
+    const float4 Wi4 = p_is_i ? WPo : WQ, Wj4 = p_is_i ? WQ : WPo;
+    const float Wi[3] = {Wi4.x, Wi4.y, Wi4.z}, Wj[3] = {Wj4.x, Wj4.y, Wj4.z};
+    // relative velocity of the image of j: peculiar difference + rate r_y x
+    const float dU[3] = {Vj.x - Vi.x + rate * rr[1], Vj.y - Vi.y, Vj.z - Vi.z};
+
+    PairOut<float> ou;
+    if (s.lubrication) {
+      const float xi_e = fmaxf(xi, xi_min);
+      const float ixi = 1.0f / xi_e;
+      const float L = __logf(ixi);
+      const Res8<float> R = resistances_f(eta, ai, aj, ixi, L);
+      float g[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (NOISE) {
+        const uint32_t li = (uint32_t)((p_is_i ? tp : tq) - t0);
+        const uint32_t lj = (uint32_t)((p_is_i ? tq : tp) - t0);
+        gauss6_f32(key0, key1, k, li, lj, g);
+      }
+      lub_brownian<float, NOISE>(R, n, dU, Wi, Wj, g, g + 3, c, tsign, ou);
+    } else {
+#pragma unroll
+      for (int q3 = 0; q3 < 3; ++q3) ou.FL[q3] = ou.FB[q3] = ou.Ti[q3] = ou.Tj[q3] = 0.f;
+    }
+    float FC[3] = {0.f, 0.f, 0.f}, TCi[3] = {0.f, 0.f, 0.f}, TCj[3] = {0.f, 0.f, 0.f};
+    if (h < 0.0f && s.contact) {
+      const float delta = -h;
+      float Ft[3] = {0.f, 0.f, 0.f};
+      if (FRIC && mu > 0.0f) {
+        float xh[3] = {0.f, 0.f, 0.f}, xl[3] = {0.f, 0.f, 0.f};
+        const int64_t hi = (int64_t)sl * Np + po;
+        if ((ocm >> sl) & 1ull) {
+#pragma unroll
+          for (int q3 = 0; q3 < 3; ++q3) {
+            const float2 v = hist[hi + q3 * hs];
+            xh[q3] = v.x; xl[q3] = v.y;
+          }
+        }
+        if (s.advance) {
+          const float ww[3] = {ai * Wi[0] + aj * Wj[0], ai * Wi[1] + aj * Wj[1],
+                               ai * Wi[2] + aj * Wj[2]};
+          float wxn[3];
+          cross3(ww, n, wxn);
+          const float v[3] = {dU[0] - wxn[0], dU[1] - wxn[1], dU[2] - wxn[2]};
+          history_update_df(xh, xl, n, v, dtf, kt, mu * kn * delta);
+        }
+#pragma unroll
+        for (int q3 = 0; q3 < 3; ++q3) hist[hi + q3 * hs] = make_float2(xh[q3], xl[q3]);
+        atomicOr(&sM[warp * 32 + o], 1ull << sl);
+        Ft[0] = kt * xh[0]; Ft[1] = kt * xh[1]; Ft[2] = kt * xh[2];
+      }
+#pragma unroll
+      for (int q3 = 0; q3 < 3; ++q3) FC[q3] = -kn * delta * n[q3] + Ft[q3];
+      float nxF[3];
+      cross3(n, Ft, nxF);
+#pragma unroll
+      for (int q3 = 0; q3 < 3; ++q3) {
+        TCi[q3] = ai * nxF[q3];
+        TCj[q3] = aj * nxF[q3];
+      }
+    }
+    float Fi[3], Ti_[3], Tj_[3];
+#pragma unroll
+    for (int q3 = 0; q3 < 3; ++q3) {
+      Fi[q3] = FC[q3] + ou.FL[q3] + ou.FB[q3];
+      Ti_[q3] = TCi[q3] + ou.Ti[q3];
+      Tj_[q3] = TCj[q3] + ou.Tj[q3];
+    }
+    // owner's share (shared memory), partner's share (vector reductions)
+    float4* so = &sF[warp * 32 + o];
+    float4* st = &sT[warp * 32 + o];
+    const float* To = p_is_i ? Ti_ : Tj_;
+    const float* Tq = p_is_i ? Tj_ : Ti_;
+    atomicAdd(&so->x, sg * Fi[0]);
+    atomicAdd(&so->y, sg * Fi[1]);
+    atomicAdd(&so->z, sg * Fi[2]);
+    atomicAdd(&st->x, To[0]);
+    atomicAdd(&st->y, To[1]);
+    atomicAdd(&st->z, To[2]);
+    red_add_v4(F4 + q, -sg * Fi[0], -sg * Fi[1], -sg * Fi[2], 0.f);
+    red_add_v4(T4 + q, Tq[0], Tq[1], Tq[2], 0.f);
+    if (SAMPLE) {
+#pragma unroll
+      for (int al = 0; al < 3; ++al)
+#pragma unroll
+        for (int be = 0; be < 3; ++be) {
+          vir[3 * al + be] += FC[al] * rr[be];
+          vir[9 + 3 * al + be] += ou.FL[al] * rr[be];
+          vir[18 + 3 * al + be] += ou.FB[al] * rr[be];
+        }
+    }
+  }
+  // the warp's own accumulators are complete once its lanes are done
+  __syncwarp();
+  if (active) {
+    const float4 f = sF[tid], t = sT[tid];
+    red_add_v4(F4 + p, f.x, f.y, f.z, 0.f);
+    red_add_v4(T4 + p, t.x, t.y, t.z, 0.f);
+    if (FRIC) A.cmsk[cur][p] = sM[tid];
+  }
+  if (SAMPLE) {
+    // single-precision warp sums into shared memory; the last warp of the
+    // block to arrive folds the eight warp sums (in warp order) into the
+    // block partial, so no warp waits at a block-wide barrier.  Blocks,
+    // replicas and time are summed in double by the reduction kernel.
+#pragma unroll
+    for (int cc = 0; cc < kPartialLen; ++cc) {
+      float x = vir[cc];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      if (lane == 0) sW[warp * kPartialLen + cc] = x;
+    }
+    __threadfence_block();
+    int arrived = 0;
+    if (lane == 0) arrived = atomicAdd(&sArrive, 1);
+    arrived = __shfl_sync(0xffffffffu, arrived, 0);
+    if (arrived == kBlock / 32 - 1) {
+      __threadfence_block();
+      if (lane < kPartialLen) {
+        float sum = 0.0f;
+        for (int w = 0; w < kBlock / 32; ++w)
+          sum += *(volatile float*)&sW[w * kPartialLen + lane];
+        A.pair_partial_w[(int64_t)b * kPartialLen + lane] = sum;
+      }
+    }
+  }
+}
+
+template <bool NOISE, bool FRIC>
+static void launch_pm(const Arrays& A, const BlockMap& bm, const StepArgs& s,
+                      cudaStream_t st) {
+  if (s.sample)
+    k_pair_mixed<NOISE, FRIC, true><<<bm.nblocks, kBlock, 0, st>>>(A, bm, s);
+  else
+    k_pair_mixed<NOISE, FRIC, false><<<bm.nblocks, kBlock, 0, st>>>(A, bm, s);
+}
+
+void launch_pair_mixed(const Arrays& A, const BlockMap& bm, const StepArgs& s, int tpp,
+                       cudaStream_t st) {
+  (void)tpp;
+  const bool noise = s.noise != 0, fric = s.friction != 0;
+  if (noise && fric) launch_pm<true, true>(A, bm, s, st);
+  else if (noise) launch_pm<true, false>(A, bm, s, st);
+  else if (fric) launch_pm<false, true>(A, bm, s, st);
+  else launch_pm<false, false>(A, bm, s, st);
+}
+
+}  // namespace susp

@@ -61,6 +61,11 @@ __global__ void k_zero_forces(Arrays A) {
   if (p >= A.N) return;
   const int cur = A.ctl->cur;
   const int64_t Np = A.Npad;
+  if (A.mixed) {
+    reinterpret_cast<float4*>(A.frc[cur])[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+    reinterpret_cast<float4*>(A.trq[cur])[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     A.frc[cur][q * Np + p] = 0.0;
@@ -75,13 +80,15 @@ __global__ void k_gather(Arrays A, int what, double* __restrict__ out) {
   const int cur = A.ctl->cur;
   const int p = A.slot_of_tag[t];
   const int64_t Np = A.Npad;
-  double v0, v1, v2;
-  if (what == 0) { const double4_32a P = A.pos[cur][p]; v0 = P.x; v1 = P.y; v2 = P.z; }
-  else if (what == 1) { const double4_32a V = A.vel[cur][p]; v0 = V.x; v1 = V.y; v2 = V.z; }
-  else if (what == 2) { const double4_32a W = A.omg[cur][p]; v0 = W.x; v1 = W.y; v2 = W.z; }
-  else if (what == 3) { const double* F = A.frc[cur]; v0 = F[p]; v1 = F[Np + p]; v2 = F[2 * Np + p]; }
-  else { const double* T = A.trq[cur]; v0 = T[p]; v1 = T[Np + p]; v2 = T[2 * Np + p]; }
-  out[3 * t] = v0; out[3 * t + 1] = v1; out[3 * t + 2] = v2;
+  double v[3];
+  if (what <= 2) {
+    const double4_32a* base = what == 0 ? A.pos[cur] : (what == 1 ? A.vel[cur] : A.omg[cur]);
+    const double4_32a r = read_rec_d(base, A.mixed, p);
+    v[0] = r.x; v[1] = r.y; v[2] = r.z;
+  } else {
+    read_vec3_d(what == 3 ? A.frc[cur] : A.trq[cur], A.mixed, Np, p, v);
+  }
+  out[3 * t] = v[0]; out[3 * t + 1] = v[1]; out[3 * t + 2] = v[2];
 }
 
 // Pairs of the live half list as (tag_i, tag_j), tag_i < tag_j, written at
@@ -106,9 +113,14 @@ __global__ void k_list_pairs(Arrays A, const long long* __restrict__ off,
     ij[2 * o + 1] = tp < tq ? tq : tp;
     if (with_history) {
       const int64_t h = (int64_t)sl * Np + p;
-      xi_t[3 * o] = A.hist[cur][h];
-      xi_t[3 * o + 1] = A.hist[cur][h + hs];
-      xi_t[3 * o + 2] = A.hist[cur][h + 2 * hs];
+      for (int c = 0; c < 3; ++c) {
+        if (A.mixed) {
+          const float2 f = reinterpret_cast<const float2*>(A.hist[cur])[h + c * hs];
+          xi_t[3 * o + c] = (double)f.x + (double)f.y;
+        } else {
+          xi_t[3 * o + c] = A.hist[cur][h + c * hs];
+        }
+      }
     }
     ++o;
   }
@@ -133,9 +145,25 @@ __global__ void k_reduce_stress(Arrays A, const int* __restrict__ rep_bstart,
   if (!is_pair && !sample_kin) return;
   const int b0 = rep_bstart[r], b1 = rep_bstart[r + 1];
   double s = 0.0;
-  for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x)
-    s += is_pair ? A.pair_partial[(int64_t)b * kPartialLen + c]
-                 : A.kin_partial[(int64_t)b * kKinLen + (c - kPartialLen)];
+  if (is_pair && A.mixed) {
+    // single-precision block partials of the mixed pair kernel, summed per
+    // thread in double-float (two-sum compensation, 48-bit significand)
+    // without FP64-pipe work, then once in double
+    float hi = 0.0f, lo = 0.0f;
+    for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
+      const float v = A.pair_partial_w[(int64_t)b * kPartialLen + c];
+      const float t = __fadd_rn(hi, v);
+      const float bb = __fsub_rn(t, hi);
+      const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(v, bb));
+      hi = t;
+      lo = __fadd_rn(lo, e);
+    }
+    s = (double)hi + (double)lo;
+  } else {
+    for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x)
+      s += is_pair ? A.pair_partial[(int64_t)b * kPartialLen + c]
+                   : A.kin_partial[(int64_t)b * kKinLen + (c - kPartialLen)];
+  }
   double v[1] = {s};
   double out[1];
   __shared__ double res;

@@ -61,7 +61,11 @@ __device__ __forceinline__ void gauss6_f64(uint32_t k0, uint32_t k1,
 }
 
 // Single-precision variant for the mixed path: 24-bit uniforms
-// u = (w >> 8 + 1/2) 2^-24 in (0, 1), fast log and sincos of 2 pi u.
+// u = (w >> 8 + 1/2) 2^-24 in (0, 1), hardware log2 and sin/cos of the
+// angle 2 pi u - pi in [-pi, pi) (the special-function unit is accurate to
+// ~1e-6 absolute on that range; cos and sin of the shifted angle are the
+// negatives of those of 2 pi u, so the deviates are negated back and follow
+// the double-precision ones to single-precision accuracy).
 __device__ __forceinline__ void gauss6_f32(uint32_t k0, uint32_t k1,
                                            long long k, uint32_t t1,
                                            uint32_t t2, float g[6]) {
@@ -76,9 +80,9 @@ __device__ __forceinline__ void gauss6_f32(uint32_t k0, uint32_t k1,
     const float ub = ((float)(w[2 * q + 1] >> 8) + 0.5f) * 5.9604644775390625e-08f;
     const float rr = sqrtf(-2.0f * __logf(ua));
     float s, c;
-    sincospif(2.0f * ub, &s, &c);
-    g[2 * q] = rr * c;
-    g[2 * q + 1] = rr * s;
+    __sincosf(6.2831853071795865f * ub - 3.14159265358979f, &s, &c);
+    g[2 * q] = -rr * c;
+    g[2 * q + 1] = -rr * s;
   }
 }
 

@@ -18,9 +18,10 @@
 //   nnb  int32  [Npad]                    row lengths
 //   hist double [3][kmax][Npad]           tangential history per slot (mu>0)
 //   cmsk uint64 [Npad]                    slot s in contact at last evaluation
-//   mirror (mixed precision)  float4 posm (dx, dy, dz, a) offset from the
-//                               home-cell origin; float4 velm (u - U_inf, _);
-//                               float4 omgm (W, _); int32 cell (home cell)
+//   mirror (mixed precision)  posm: two float4 (hi, lo) of (dx, dy, dz, a),
+//                               the offset from the home-cell origin;
+//                               float4 velm (u - U_inf, tag); float4 omgm
+//                               (W, packed home cell); int32 cell (home key)
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -56,11 +57,68 @@ struct Replica {
   int32_t pad0;
   int64_t cell_base; // first cell key of this replica
   int64_t p0, n;     // particle range (tags and sorted order)
+  // single-precision and double-float copies for the mixed path; the
+  // strain-dependent ones are refreshed by refresh_strain_fields()
+  float rate_f, noise_cf, eta_f, kn_f, kt_f, mu_f;
+  float cwf[3];                 // cell widths L / nc
+  float ctilt_f;                // current tilt / ncy
+  float L_hi[3], L_lo[3];       // box edges
+  float yc_hi, yc_lo;           // Ly / 2
+  float dux_hi, dux_lo;         // rate * Ly: velocity jump across y
+  float rate_hi, rate_lo;
+  float cw_hi[3], cw_lo[3];     // cell widths
+  float ct_hi, ct_lo;           // current tilt / ncy
+  float nt_hi, nt_lo;           // tilt after the next strain advance
+  float nct_hi, nct_lo;         // that tilt / ncy
+  float pad1[2];
 };
+
+// Next strain of the box with the flip of Sec. II.E.
+__host__ __device__ __forceinline__ double advance_strain(double st, double rate_dt,
+                                                          double flip_at, double flip_by) {
+  st = st + rate_dt;
+  if (st > flip_at) st = st - flip_by;
+  return st;
+}
+
+__host__ __device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+
+// Strain-dependent single/double-float fields of the mixed path.
+__host__ __device__ inline void refresh_strain_fields(Replica& R) {
+  R.ctilt_f = (float)(R.tilt * R.hcell[1]);
+  split_df(R.tilt * R.hcell[1], R.ct_hi, R.ct_lo);
+  const double nst = advance_strain(R.strain, R.rate_dt, R.flip_at, R.flip_by);
+  const double ntilt = nst * R.L[1];
+  split_df(ntilt, R.nt_hi, R.nt_lo);
+  split_df(ntilt * R.hcell[1], R.nct_hi, R.nct_lo);
+}
+
+// Constant single/double-float fields of the mixed path.
+inline void refresh_constant_fields(Replica& R) {
+  R.rate_f = (float)R.rate;
+  R.noise_cf = (float)R.noise_c;
+  R.eta_f = (float)R.eta;
+  R.kn_f = (float)R.kn;
+  R.kt_f = (float)R.kt;
+  R.mu_f = (float)R.mu;
+  for (int d = 0; d < 3; ++d) {
+    R.cwf[d] = (float)(R.L[d] * R.hcell[d]);
+    split_df(R.L[d], R.L_hi[d], R.L_lo[d]);
+    split_df(R.L[d] * R.hcell[d], R.cw_hi[d], R.cw_lo[d]);
+  }
+  split_df(0.5 * R.L[1], R.yc_hi, R.yc_lo);
+  split_df(R.rate * R.L[1], R.dux_hi, R.dux_lo);
+  split_df(R.rate, R.rate_hi, R.rate_lo);
+  refresh_strain_fields(R);
+}
 
 struct Ctl {
   long long k;                  // evaluation index of the forces held
   unsigned long long vmax_bits; // max peculiar speed of this step (double bits)
+  unsigned int vmax_fbits;      // same, single precision bits (mixed path)
   double disp_bound;            // accumulated displacement bound D
   double t_since_build;
   int need_rebuild;
@@ -88,11 +146,18 @@ struct Pair2 {
   __host__ __device__ T* operator[](int i) const { return a[i]; }
 };
 
+// Mixed-precision layout (Arrays::mixed = 1): the 32-byte records of
+// pos/vel/omg hold two float4 halves (hi, lo) of a double-float value:
+//   pos = {x_hi, y_hi, z_hi, a}{x_lo, y_lo, z_lo, 0}
+//   vel = {U_hi.., 1/m}{U_lo.., 0}      omg = {W_hi.., 1/I}{W_lo.., 0}
+// frc/trq hold float4 accumulators (F, 0) / (T, 0); hist holds float2
+// (hi, lo) per component at the double index of the FP64 layout.
 struct Arrays {
   int64_t N;        // total particles
   int64_t Npad;     // padded stride of SoA arrays
   int kmax;
   int R;
+  int mixed;        // 1: mixed-precision layout
   Pair2<double4_32a> pos, vel, omg;
   Pair2<double> frc, trq;
   Pair2<int> tag, rep;
@@ -114,6 +179,7 @@ struct Arrays {
   int64_t ncell;
   // reductions
   double* pair_partial; // [nblocks][27]
+  float* pair_partial_w; // [nblocks][27] single-precision (mixed path)
   double* kin_partial;  // [nblocks][18]
   double* stress_acc;   // [R][48]: 27 pair, 18 kinetic, pair / kinetic counts
   int* rep_bstart;      // [R + 1] first block of each replica
@@ -131,6 +197,8 @@ struct StepArgs {
   int noise, lubrication, onebody, contact, friction;
   int advance;       // 1: time advanced since the previous evaluation
   int sample;        // 1: accumulate stresses at this evaluation
+  // single-precision copies for the mixed path (set on the host)
+  float dt_f, hdt_f, xi_min_f, xi_max_f, tsign_f;
 };
 
 // ---- host-side launchers (defined in the .cu files) ----------------------
@@ -162,6 +230,10 @@ void launch_load_state(const Arrays& A, const double* x, const double* U,
                        const double* W, const double* radius,
                        const double* mass, const double* inertia,
                        const int* rep_of, cudaStream_t st);
+void launch_load_state_mixed(const Arrays& A, const double* x, const double* U,
+                             const double* W, const double* radius,
+                             const double* mass, const double* inertia,
+                             const int* rep_of, cudaStream_t st);
 void launch_zero_forces(const Arrays& A, cudaStream_t st);
 void launch_gather(const Arrays& A, int what, double* out, cudaStream_t st);
 void launch_row_counts(const Arrays& A, int with_history, long long* cnt,

@@ -1,0 +1,123 @@
+"""Mixed-precision path against the FP64 path of the same library (which is
+itself pinned to the oracle to 1e-11).
+
+With the noise switched off both paths integrate the same deterministic
+equations; the mixed one forms pair quantities in single precision
+(relative rounding ~6e-8, a few ulps through the resistances) on gaps that
+carry ~1e-7 absolute error, and accumulates forces in single precision.  One
+evaluation therefore agrees to ~1e-5 of the largest force; short
+trajectories agree to the same order.  With noise on the two paths draw the
+same Philox words but map them to Gaussians in different precision, so they
+are compared statistically (temperature) rather than element by element."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+RTOL_MIXED = 2e-5
+
+
+@pytest.fixture(scope="module")
+def susp():
+    import paper_2307_13802_gb300 as s
+    return s
+
+
+def _sys(susp, w, precision, **kw):
+    p = dict(w.params)
+    args = dict(precision=precision, eta=p["eta"], rho=p["rho"], kn=p["kn"], kt=p["kt"],
+                mu=p["mu"], xi_min=p["xi_min"], xi_max=p["xi_max"], skin=p["skin"],
+                shear_rate=p["shear_rate"], kT=p["kT"], seed=p["seed"],
+                torque_sign=p["torque_sign"], dt=p["dt"])
+    args.update(kw)
+    return susp.System(w.radii, w.box, **args)
+
+
+def _relerr(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.mark.parametrize("strain", [0.0, 0.2, -0.45])
+@pytest.mark.parametrize("poly", [False, True])
+def test_mixed_one_evaluation_without_noise(susp, strain, poly):
+    w = workloads.make(3000, 0.58, 1000.0, 1.0, poly=poly, pack_seed=51, dyn_seed=52)
+    w.x = w.x * 0.99
+    w.L = w.L * 0.99
+    res = {}
+    for prec in ("fp64", "mixed"):
+        g = _sys(susp, w, prec, noise=0)
+        g.set_state(w.x, w.U, w.W)
+        g.set_clock(3, strain)
+        g.evaluate()
+        res[prec] = (g.forces(), g.stress())
+    (F64, T64), s64 = res["fp64"]
+    (F32, T32), s32 = res["mixed"]
+    assert _relerr(F32, F64) <= RTOL_MIXED
+    assert _relerr(T32, T64) <= RTOL_MIXED
+    for key in ("contact", "lubrication"):
+        assert _relerr(s32[key], s64[key]) <= RTOL_MIXED, key
+
+
+@pytest.mark.parametrize("start_strain", [0.1, 0.495])
+def test_mixed_trajectory_tracks_fp64_without_noise(susp, start_strain):
+    # 400 steps with rebuilds (and, from 0.495, a strain flip)
+    w = workloads.make(4000, 0.56, 1000.0, 1.0, pack_seed=61, dyn_seed=62)
+    p = w.params
+    out = {}
+    for prec in ("fp64", "mixed"):
+        g = _sys(susp, w, prec, noise=0)
+        g.set_state(w.x, w.U, w.W)
+        g.set_clock(0, start_strain)
+        g.step(400, p["shear_rate"], 0.0, p["dt"], p["seed"])
+        out[prec] = (g.state(), g.forces(), g.info())
+    (x64, U64, W64), (F64, _), i64 = out["fp64"]
+    (x32, U32, W32), (F32, _), i32 = out["mixed"]
+    assert i32["nbuilds"] >= 2
+    assert i32["strain"] == pytest.approx(i64["strain"], abs=1e-12)
+    if start_strain > 0.49:
+        assert i32["strain"] < 0
+    dx = x32 - x64
+    dx -= np.rint(dx / w.L) * w.L
+    assert np.abs(dx).max() < 1e-6
+    assert np.abs(U32 - U64).max() < 1e-3 * np.abs(U64).max()
+    assert _relerr(F32, F64) <= 1e-3
+
+
+def test_mixed_state_round_trip_keeps_double_precision(susp):
+    # positions and velocities survive the double-float storage to ~1e-14
+    w = workloads.make(2000, 0.5, 10.0, 0.0, pack_seed=71)
+    g = _sys(susp, w, "mixed")
+    rng = np.random.default_rng(1)
+    U = rng.normal(size=(w.N, 3))
+    W = rng.normal(size=(w.N, 3))
+    g.set_state(w.x, U, W)
+    x2, U2, W2 = g.state()
+    assert np.abs(x2 - w.x).max() <= 1e-13 * w.L
+    assert np.abs(U2 - U).max() <= 1e-13
+    assert np.abs(W2 - W).max() <= 1e-13
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_equipartition_at_rest(susp, precision):
+    # no shear: full-step kinetic temperature equals kT (exact for the
+    # Velocity-Verlet Langevin map with FDT-consistent noise in a frozen
+    # configuration; within statistics and the O(dt) drift of the
+    # configuration here)
+    w = workloads.make(20000 if precision == "mixed" else 4000, 0.45, 1.0, 0.0,
+                       pack_seed=81, dyn_seed=82, rate=0.0)
+    p = w.params
+    kT = 1.0
+    g = _sys(susp, w, precision, shear_rate=0.0)
+    g.set_state(w.x, np.zeros_like(w.x), np.zeros_like(w.x))
+    # the configuration needs ~2 time units to forget the athermal packing
+    g.step(20000, 0.0, kT, p["dt"], 5)
+    g.stress()
+    g.step(20000, 0.0, kT, p["dt"], 5)
+    s = g.stress()
+    V = w.L ** 3
+    Tt = np.trace(s["kinetic"]) * V / (3 * w.N)
+    Tr = np.trace(s["kinetic_rot"]) * V / (3 * w.N)
+    assert Tt == pytest.approx(kT, rel=0.015)
+    assert Tr == pytest.approx(kT, rel=0.015)

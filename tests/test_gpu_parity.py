@@ -162,26 +162,6 @@ def test_friction_history_parity(susp):
     assert _relerr(F, Fo) <= 1e-7 and _relerr(T, To) <= 1e-7
 
 
-def test_mixed_precision_one_evaluation(susp):
-    w = workloads.make(3000, 0.58, 1000.0, 1.0, pack_seed=51, dyn_seed=52)
-    w.x = w.x * 0.99
-    w.L = w.L * 0.99
-    res = {}
-    for prec in ("fp64", "mixed"):
-        g = _gpu_system(susp, w, precision=prec)
-        g.set_state(w.x, w.U, w.W)
-        g.set_clock(3, 0.2)
-        g.evaluate()
-        res[prec] = (g.forces(), g.stress())
-    (F64, T64), s64 = res["fp64"]
-    (F32, T32), s32 = res["mixed"]
-    # single-precision pair arithmetic: ~1e-6 of the largest force
-    assert _relerr(F32, F64) <= 2e-5
-    assert _relerr(T32, T64) <= 2e-5
-    for key in ("contact", "lubrication"):
-        assert _relerr(s32[key], s64[key]) <= 2e-5, key
-
-
 def test_errors_are_reported(susp):
     w = workloads.make(500, 0.5, 10.0, 0.0, pack_seed=61)
     g = _gpu_system(susp, w, kmax=2)
