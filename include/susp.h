@@ -123,7 +123,8 @@ void susp_destroy(susp_t* h);
  * is owned by the handle and valid until its next call. */
 const char* susp_last_error(const susp_t* h);
 
-/* Message of the last susp_create*() failure in this thread. */
+/* Message of the last susp_create*() or susp_pair_stress_noalloc() failure in
+ * this thread. */
 const char* susp_create_error(void);
 
 /* ---- plumbing ----------------------------------------------------------- */
@@ -231,6 +232,46 @@ int susp_get_history(susp_t* h, int32_t* ij, double* xi_t, int64_t cap,
  * kernels of each rebuild taken inside a replay). */
 #define SUSP_INFO_LEN 14
 int susp_get_info(susp_t* h, double* info);
+
+/* ---- without allocation ------------------------------------------------------ */
+/* The paper has no counterpart to this call; it is a service for callers
+ * that cannot allocate device memory where they need the answer (code
+ * running inside another framework's memory arena, threads that must not
+ * touch the allocator, tools that only borrow buffers they do not own).
+ *
+ * Pair stresses of one evaluation, (1/V) sum over the listed pairs of
+ * F_{i<-j} (x) r_ij for the contact (normal part), lubrication and pair
+ * Brownian terms, computed as the double-precision evaluation of a handle
+ * does but with the tangential history taken as zero, and written to
+ * stress_out[27] (row-major 3x3 blocks in the order contact, lubrication,
+ * Brownian, like out[0..26] of susp_stress() after one sampled
+ * evaluation).  Every pointer except box and p is a DEVICE pointer of the
+ * current device and stays owned by the caller: x, U, Omega [N][3]
+ * (positions wrapped into the box), radii [N], ij [npairs][2] (pairs by
+ * index, either order; pairs beyond the lubrication cutoff add nothing),
+ * stress_out [27].  p supplies eta, kn, xi_min, xi_max, shear_rate, kT,
+ * torque_sign, seed and the noise/lubrication/contact switches; strain is
+ * the box strain, dt the timestep and k the noise counter.  Work is
+ * enqueued on `stream` (a cudaStream_t, NULL = the legacy default stream)
+ * and the call returns without waiting for it.
+ *
+ * The call allocates nothing: its scratch is a fixed array in device memory
+ * that every GPU which loads the library holds until the process exits.
+ * npairs above SUSP_NOALLOC_MAX_PAIRS is rejected with SUSP_EINVAL.  The
+ * first call on each device looks up that array's device address (with the
+ * device current), so make the first call before any stream capture.  All
+ * calls share the array: calls whose work overlaps on the GPU (several
+ * streams, or several host threads) race and give wrong results; calls on
+ * one stream are ordered and safe.  Errors: SUSP_EINVAL (NULL pointer,
+ * N <= 0, npairs out of range, dt <= 0, kT < 0, box <= 0), SUSP_ENODEV,
+ * SUSP_ECUDA; the message is read with susp_create_error(). */
+#define SUSP_NOALLOC_MAX_PAIRS (1 << 21)
+int susp_pair_stress_noalloc(int64_t N, const double* x, const double* U,
+                             const double* Omega, const double* radii,
+                             int64_t npairs, const int32_t* ij,
+                             const double box[3], double strain,
+                             const susp_params* p, double dt, int64_t k,
+                             double* stress_out, void* stream);
 
 /* ---- checkpoint ------------------------------------------------------------- */
 /* Writes / reads positions, velocities, forces, tangential history, k,

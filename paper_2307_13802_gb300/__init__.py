@@ -82,6 +82,10 @@ _SIGNATURES = {
     "susp_get_pairs": (C.c_int, [_H, _I32, C.c_int64, _I64]),
     "susp_get_history": (C.c_int, [_H, _I32, _D, C.c_int64, _I64]),
     "susp_get_info": (C.c_int, [_H, _D]),
+    "susp_pair_stress_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.c_void_p, C.c_int64, C.c_void_p, _D,
+                                           C.c_double, C.POINTER(susp_params), C.c_double,
+                                           C.c_int64, C.c_void_p, C.c_void_p]),
     "susp_save": (C.c_int, [_H, C.c_char_p]),
     "susp_load": (C.c_int, [_H, C.c_char_p]),
 }

@@ -29,6 +29,7 @@ UNITS = [
     ("k_util.cu", ["-fmad=false"]),
     ("k_mixed.cu", ["-fmad=true"]),
     ("k_pair_mixed.cu", ["-fmad=true", "-prec-div=false", "-prec-sqrt=false"]),
+    ("noalloc.cu", ["-fmad=false"]),
 ]
 
 

@@ -29,6 +29,11 @@ struct GraphChunk {
 
 }  // namespace
 
+namespace susp {
+// message of the last failing call that has no handle
+void set_handleless_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace susp
+
 struct susp_s {
   int dev = 0;
   int R = 1;
