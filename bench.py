@@ -235,8 +235,9 @@ def run_ours(args, rank, world, local_rank, dist):
         kernel = {"pair": "k_pair_mixed" if args.precision == "mixed" else "k_pair_fp64",
                   "integrate": "k_integrate_mixed" if args.precision == "mixed" else "k_integrate_fp64",
                   "finalize": "k_finalize"}.get(fam, fam)
-        src = "k_mixed.cu" if args.precision == "mixed" else (
-            "k_pair_fp64.cu" if fam == "pair" else "k_integrate_fp64.cu")
+        src = {("mixed", "pair"): "k_pair_mixed.cu", ("mixed", "integrate"): "k_mixed.cu",
+               ("fp64", "pair"): "k_pair_fp64.cu"}.get((args.precision, fam),
+                                                       "k_integrate_fp64.cu")
         rec = NCU_TRAFFIC.get(kernel)
         traffic = None
         if rec and rec.get("source_sha") == _src_hash(src):

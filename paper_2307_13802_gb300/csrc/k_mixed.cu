@@ -132,7 +132,12 @@ __device__ void epilogue_mixed(const Arrays& A, const StepArgs& s,
   ctl->ticket = 0u;
 }
 
-__global__ void __launch_bounds__(kBlock)
+// resident blocks per SM the register allocation targets
+#ifndef SUSP_INTEG_MINBLOCKS
+#define SUSP_INTEG_MINBLOCKS 4
+#endif
+
+__global__ void __launch_bounds__(kBlock, SUSP_INTEG_MINBLOCKS)
 k_integrate_mixed(Arrays A, BlockMap bm, StepArgs s, int close, int sample_kin,
                   unsigned long long cond_handle, int use_cond, float dt_hi, float dt_lo,
                   float hdt) {
@@ -161,6 +166,8 @@ k_integrate_mixed(Arrays A, BlockMap bm, StepArgs s, int close, int sample_kin,
     float4* F4 = reinterpret_cast<float4*>(A.frc[cur]);
     float4* T4 = reinterpret_cast<float4*>(A.trq[cur]);
     const float4 f = F4[p], t = T4[p];
+    const int cellkey = A.cell[p];     // issued with the other loads
+    const int tagp = A.tag[cur][p];
     const float cm = hdt * im, cI = hdt * iI;
     if (close) {
       kick(U, f, cm);
@@ -194,7 +201,7 @@ k_integrate_mixed(Arrays A, BlockMap bm, StepArgs s, int close, int sample_kin,
     F4[p] = make_float4(0.f, 0.f, 0.f, 0.f);
     T4[p] = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 pm[2], vm, om;
-    make_mirrors(RP, tilt, ct, A.cell[p], x, df{a, alo}, U, W, A.tag[cur][p], pm, vm, om);
+    make_mirrors(RP, tilt, ct, cellkey, x, df{a, alo}, U, W, tagp, pm, vm, om);
     A.posm[2 * p] = pm[0];
     A.posm[2 * p + 1] = pm[1];
     A.velm[p] = vm;

@@ -113,8 +113,14 @@ __device__ __forceinline__ int wrap_dc(int d, int n) {
   return d > 1 ? d - n : (d < -1 ? d + n : d);
 }
 
+// resident blocks per SM the register allocation targets (3 measured
+// fastest at N = 1M: 80 registers with a few bytes of spill beat 124 at 2)
+#ifndef SUSP_PAIR_MINBLOCKS
+#define SUSP_PAIR_MINBLOCKS 3
+#endif
+
 template <bool NOISE, bool FRIC, bool SAMPLE>
-__global__ void __launch_bounds__(kBlock, 2)
+__global__ void __launch_bounds__(kBlock, SUSP_PAIR_MINBLOCKS)
 k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   __shared__ float4 sF[kBlock];
   __shared__ float4 sT[kBlock];
@@ -200,51 +206,26 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
 #pragma unroll
   for (int q = 0; q < (SAMPLE ? kPartialLen : 1); ++q) vir[q] = 0.0f;
 
-  for (int base = 0; base < total; base += 32) {
-    const int t = base + lane;
-    // owner lane: first lane whose inclusive row end exceeds t
-    int o = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-      const int v = __shfl_sync(0xffffffffu, incl, o + step - 1);
-      if (v <= t) o += step;
-    }
-    const int oexcl = __shfl_sync(0xffffffffu, excl, o);
-    const unsigned long long ocm = FRIC ? __shfl_sync(0xffffffffu, cm_own, o) : 0ull;
-    if (t >= total) continue;
-    const int sl = t - oexcl;
+  // Pairs within the cutoff are queued per warp in shared memory and the
+  // pair physics runs on full 32-lane batches of that queue, so lanes whose
+  // item falls beyond the cutoff do not idle through it.
+  constexpr int kQ = 64;
+  __shared__ int qQ[kBlock / 32][kQ];
+  __shared__ int qM[kBlock / 32][kQ];        // owner lane | slot << 5 | had contact << 12
+  __shared__ float qG[kBlock / 32][6][kQ];   // r_x, r_y, r_z, d, h, S
+  int qn = 0;
+
+  auto pair_physics = [&](int e) {
+    const int q = qQ[warp][e];
+    const int meta = qM[warp][e];
+    const int o = meta & 31, sl = (meta >> 5) & 127;
+    const bool had = (meta >> 12) & 1;
+    const float rpq[3] = {qG[warp][0][e], qG[warp][1][e], qG[warp][2][e]};
+    const float d = qG[warp][3][e], h = qG[warp][4][e], S = qG[warp][5][e];
+    const float xi = 2.0f * h / S;
     const int po = pb + warp * 32 + o;
-    const int q = __ldg(nbr + (int64_t)sl * Np + po);
     const float4 P = __ldg(PM + 2 * po), Q = __ldg(PM + 2 * q);
     const float4 WPo = __ldg(OM + po), WQ = __ldg(OM + q);
-    int pcx, pcy, pcz, qcx, qcy, qcz;
-    unpack_cell(__float_as_int(WPo.w), pcx, pcy, pcz);
-    unpack_cell(__float_as_int(WQ.w), qcx, qcy, qcz);
-    const int dcx = wrap_dc(qcx - pcx, ncx), dcy = wrap_dc(qcy - pcy, ncy),
-              dcz = wrap_dc(qcz - pcz, ncz);
-    float rpq[3];
-    rpq[0] = (Q.x - P.x) + (cwx * (float)dcx + ctilt * (float)dcy);
-    rpq[1] = (Q.y - P.y) + cwy * (float)dcy;
-    rpq[2] = (Q.z - P.z) + cwz * (float)dcz;
-    const float d2f = rpq[0] * rpq[0] + rpq[1] * rpq[1] + rpq[2] * rpq[2];
-    const float rc = (P.w + Q.w) * rc_fac;
-    // beyond the lubrication cutoff (with a margin for single-precision
-    // rounding; the exact test follows): no force, no contact
-    if (d2f > rc * rc * 1.00001f) continue;
-    // separation and gap in double-float: h = (d^2 - S^2) / (d + S)
-    const float4 Pl = __ldg(PM + 2 * po + 1), Ql = __ldg(PM + 2 * q + 1);
-    const df rx = df_add(df_diff(Q.x, Ql.x, P.x, Pl.x),
-                         df_add(df_mul_f(cw0, (float)dcx), df_mul_f(ct_df, (float)dcy)));
-    const df ry = df_add(df_diff(Q.y, Ql.y, P.y, Pl.y), df_mul_f(cw1, (float)dcy));
-    const df rz = df_add(df_diff(Q.z, Ql.z, P.z, Pl.z), df_mul_f(cw2, (float)dcz));
-    const df dd = df_add(df_add(df_mul(rx, rx), df_mul(ry, ry)), df_mul(rz, rz));
-    const df Sd = df_add(df{P.w, Pl.w}, df{Q.w, Ql.w});
-    const float S = Sd.hi;
-    const float d = sqrtf(dd.hi);
-    const float h = df_to_f(df_sub(dd, df_mul(Sd, Sd))) / (d + S);
-    const float xi = 2.0f * h / S;
-    if (xi > xi_max) continue;
-    rpq[0] = df_to_f(rx); rpq[1] = df_to_f(ry); rpq[2] = df_to_f(rz);
     const float4 VPo = __ldg(VM + po), VQ = __ldg(VM + q);
     const int tp = __float_as_int(VPo.w), tq = __float_as_int(VQ.w);
     const bool p_is_i = tp < tq;
@@ -283,7 +264,7 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
       if (FRIC && mu > 0.0f) {
         float xh[3] = {0.f, 0.f, 0.f}, xl[3] = {0.f, 0.f, 0.f};
         const int64_t hi = (int64_t)sl * Np + po;
-        if ((ocm >> sl) & 1ull) {
+        if (had) {
 #pragma unroll
           for (int q3 = 0; q3 < 3; ++q3) {
             const float2 v = hist[hi + q3 * hs];
@@ -343,7 +324,75 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
           vir[18 + 3 * al + be] += ou.FB[al] * rr[be];
         }
     }
+  };
+
+  for (int base = 0; base < total; base += 32) {
+    const int t = base + lane;
+    // owner lane: first lane whose inclusive row end exceeds t
+    int o = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int v = __shfl_sync(0xffffffffu, incl, o + step - 1);
+      if (v <= t) o += step;
+    }
+    const int oexcl = __shfl_sync(0xffffffffu, excl, o);
+    const unsigned long long ocm = FRIC ? __shfl_sync(0xffffffffu, cm_own, o) : 0ull;
+    bool keep = false;
+    int q = 0, sl = 0;
+    float gq[6];
+    if (t < total) {
+      sl = t - oexcl;
+      const int po = pb + warp * 32 + o;
+      q = __ldg(nbr + (int64_t)sl * Np + po);
+      const float4 P = __ldg(PM + 2 * po), Q = __ldg(PM + 2 * q);
+      int pcx, pcy, pcz, qcx, qcy, qcz;
+      unpack_cell(__float_as_int(__ldg(&OM[po].w)), pcx, pcy, pcz);
+      unpack_cell(__float_as_int(__ldg(&OM[q].w)), qcx, qcy, qcz);
+      const int dcx = wrap_dc(qcx - pcx, ncx), dcy = wrap_dc(qcy - pcy, ncy),
+                dcz = wrap_dc(qcz - pcz, ncz);
+      const float r0 = (Q.x - P.x) + (cwx * (float)dcx + ctilt * (float)dcy);
+      const float r1 = (Q.y - P.y) + cwy * (float)dcy;
+      const float r2 = (Q.z - P.z) + cwz * (float)dcz;
+      const float d2f = r0 * r0 + r1 * r1 + r2 * r2;
+      const float rc = (P.w + Q.w) * rc_fac;
+      // beyond the lubrication cutoff (with a margin for single-precision
+      // rounding; the exact test follows): no force, no contact
+      if (d2f <= rc * rc * 1.00001f) {
+        // separation and gap in double-float: h = (d^2 - S^2) / (d + S)
+        const float4 Pl = __ldg(PM + 2 * po + 1), Ql = __ldg(PM + 2 * q + 1);
+        const df rx = df_add(df_diff(Q.x, Ql.x, P.x, Pl.x),
+                             df_add(df_mul_f(cw0, (float)dcx), df_mul_f(ct_df, (float)dcy)));
+        const df ry = df_add(df_diff(Q.y, Ql.y, P.y, Pl.y), df_mul_f(cw1, (float)dcy));
+        const df rz = df_add(df_diff(Q.z, Ql.z, P.z, Pl.z), df_mul_f(cw2, (float)dcz));
+        const df dd = df_add(df_add(df_mul(rx, rx), df_mul(ry, ry)), df_mul(rz, rz));
+        const df Sd = df_add(df{P.w, Pl.w}, df{Q.w, Ql.w});
+        const float S = Sd.hi;
+        const float d = sqrtf(dd.hi);
+        const float h = df_to_f(df_sub(dd, df_mul(Sd, Sd))) / (d + S);
+        if (2.0f * h / S <= xi_max) {
+          keep = true;
+          gq[0] = df_to_f(rx); gq[1] = df_to_f(ry); gq[2] = df_to_f(rz);
+          gq[3] = d; gq[4] = h; gq[5] = S;
+        }
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (keep) {
+      const int e = qn + __popc(m & ((1u << lane) - 1u));
+      qQ[warp][e] = q;
+      qM[warp][e] = o | (sl << 5) | ((FRIC && ((ocm >> sl) & 1ull)) ? (1 << 12) : 0);
+#pragma unroll
+      for (int c6 = 0; c6 < 6; ++c6) qG[warp][c6][e] = gq[c6];
+    }
+    qn += __popc(m);
+    __syncwarp();
+    if (qn >= 32) {
+      pair_physics(qn - 32 + lane);
+      qn -= 32;
+      __syncwarp();
+    }
   }
+  if (lane < qn) pair_physics(lane);
   // the warp's own accumulators are complete once its lanes are done
   __syncwarp();
   if (active) {
