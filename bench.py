@@ -131,7 +131,7 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
-# algorithmic bytes per sphere of each kernel family (see DESIGN.md)
+# algorithmic bytes per sphere of each kernel family
 # ---------------------------------------------------------------------------
 def algorithmic_bytes(family: str, precision: str, K: float, c: float, fric: bool) -> float:
     """Bytes each launch must move per sphere: every record read or written

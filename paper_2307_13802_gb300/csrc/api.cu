@@ -751,6 +751,267 @@ int list_pairs(susp_t* h, int with_history, int32_t* ij, double* xi, int64_t cap
   return SUSP_OK;
 }
 
+int set_state_impl(susp_t* h, const double* x, const double* U, const double* W,
+                          cudaMemcpyKind kind) {
+  if (!h) return SUSP_EINVAL;
+  h->err.clear();
+  if (!x) return fail(h, SUSP_EINVAL, "positions are required");
+  int rc = allocate(h);
+  if (rc) return rc;
+  CK(cudaSetDevice(h->dev));
+  const size_t bytes = sizeof(double) * 3 * h->N;
+  double* dx = h->d_stage;
+  double* dU = U ? h->d_stage + 3 * h->N : nullptr;
+  double* dW = W ? h->d_stage + 6 * h->N : nullptr;
+  CK(cudaMemcpyAsync(dx, x, bytes, kind, h->stream));
+  if (U) CK(cudaMemcpyAsync(dU, U, bytes, kind, h->stream));
+  if (W) CK(cudaMemcpyAsync(dW, W, bytes, kind, h->stream));
+  // strain/tilt must be current before wrapping
+  rc = sync_replicas(h, h->last_dt);
+  if (rc) return rc;
+  (h->p0.precision == SUSP_MIXED ? launch_load_state_mixed : launch_load_state)(
+      h->A, dx, dU, dW, h->d_radius, h->d_mass, h->d_inertia, h->d_rep_of,
+                    h->stream);
+  launch_request_rebuild(h->A, h->stream);
+  h->have_state = true;
+  h->forces_valid = false;
+  return check_errors(h);
+}
+
+// ---------------------------------------------------------------------------
+// checkpoints
+// ---------------------------------------------------------------------------
+// File layout (native byte order, written by this library only):
+//   "SUSPCKP1", int64 N, int32 R, int32 precision, int64 k, int64 steps_done,
+//   double last_dt, int32 forces_valid, int32 0,
+//   R x susp_params, R x double strain, N x double radius,
+//   5 x [N][3] double: x, U, Omega, F, T (tag order),
+//   R x 48 double stress accumulators,
+//   int64 npairs, npairs x (int32 tag_i, int32 tag_j), npairs x 3 double xi_t,
+//   "SUSPEND1".
+// The mixed layout's double-float values convert to and from double exactly.
+constexpr char kCkMagic[8] = {'S', 'U', 'S', 'P', 'C', 'K', 'P', '1'};
+constexpr char kCkEnd[8] = {'S', 'U', 'S', 'P', 'E', 'N', 'D', '1'};
+
+struct CkHeader {
+  char magic[8];
+  int64_t N;
+  int32_t R, precision;
+  int64_t k, steps_done;
+  double last_dt;
+  int32_t forces_valid, pad;
+};
+
+bool same_static_params(const susp_params& a, const susp_params& b) {
+  return a.eta == b.eta && a.rho == b.rho && a.kn == b.kn && a.kt == b.kt && a.mu == b.mu &&
+         a.xi_min == b.xi_min && a.xi_max == b.xi_max && a.skin == b.skin &&
+         a.torque_sign == b.torque_sign && a.precision == b.precision && a.noise == b.noise &&
+         a.lubrication == b.lubrication && a.onebody == b.onebody && a.contact == b.contact &&
+         a.sample_every == b.sample_every;
+}
+
+struct FileCloser {
+  FILE* f;
+  ~FileCloser() { if (f) std::fclose(f); }
+};
+
+int save_checkpoint(susp_t* h, const char* path) {
+  const int64_t N = h->N;
+  std::vector<double> st(15 * N);
+  int rc = SUSP_OK;
+  for (int w = 0; w < 5 && !rc; ++w) rc = gather_host(h, w, st.data() + 3 * N * w);
+  if (rc) return rc;
+  int64_t np = 0;
+  rc = list_pairs(h, 1, nullptr, nullptr, 0, &np);
+  if (rc) return rc;
+  std::vector<int32_t> ij(2 * std::max<int64_t>(np, 1));
+  std::vector<double> xi(3 * std::max<int64_t>(np, 1));
+  if (np > 0) {
+    int64_t np2 = 0;
+    rc = list_pairs(h, 1, ij.data(), xi.data(), np, &np2);
+    if (rc) return rc;
+  }
+  Ctl c{};
+  std::vector<Replica> rep(h->R);
+  std::vector<double> acc(48 * (size_t)h->R);
+  CK(cudaMemcpyAsync(&c, h->A.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(rep.data(), h->A.repl, sizeof(Replica) * h->R, cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaMemcpyAsync(acc.data(), h->A.stress_acc, sizeof(double) * acc.size(),
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  CkHeader hd{};
+  std::memcpy(hd.magic, kCkMagic, 8);
+  hd.N = N;
+  hd.R = h->R;
+  hd.precision = h->p0.precision;
+  hd.k = c.k;
+  hd.steps_done = h->steps_done;
+  hd.last_dt = h->last_dt;
+  hd.forces_valid = h->forces_valid ? 1 : 0;
+  std::vector<double> strain(h->R);
+  for (int r = 0; r < h->R; ++r) strain[r] = rep[r].strain;
+  FileCloser fc{std::fopen(path, "wb")};
+  if (!fc.f) return fail(h, SUSP_EINVAL, std::string("cannot open ") + path + " for writing");
+  bool ok = std::fwrite(&hd, sizeof hd, 1, fc.f) == 1;
+  ok = ok && std::fwrite(h->pr.data(), sizeof(susp_params), h->R, fc.f) == (size_t)h->R;
+  ok = ok && std::fwrite(strain.data(), sizeof(double), h->R, fc.f) == (size_t)h->R;
+  ok = ok && std::fwrite(h->radii.data(), sizeof(double), N, fc.f) == (size_t)N;
+  ok = ok && std::fwrite(st.data(), sizeof(double), st.size(), fc.f) == st.size();
+  ok = ok && std::fwrite(acc.data(), sizeof(double), acc.size(), fc.f) == acc.size();
+  ok = ok && std::fwrite(&np, sizeof np, 1, fc.f) == 1;
+  ok = ok && std::fwrite(ij.data(), sizeof(int32_t), 2 * np, fc.f) == (size_t)(2 * np);
+  ok = ok && std::fwrite(xi.data(), sizeof(double), 3 * np, fc.f) == (size_t)(3 * np);
+  ok = ok && std::fwrite(kCkEnd, 1, 8, fc.f) == 8;
+  ok = (std::fflush(fc.f) == 0) && ok;
+  if (!ok) return fail(h, SUSP_EINVAL, std::string("write to ") + path + " failed");
+  return SUSP_OK;
+}
+
+int load_checkpoint(susp_t* h, const char* path) {
+  FileCloser fc{std::fopen(path, "rb")};
+  if (!fc.f) return fail(h, SUSP_EINVAL, std::string("cannot open ") + path);
+  auto bad = [&](const char* what) {
+    return fail(h, SUSP_EINVAL, std::string("checkpoint ") + path + ": " + what);
+  };
+  CkHeader hd{};
+  if (std::fread(&hd, sizeof hd, 1, fc.f) != 1 || std::memcmp(hd.magic, kCkMagic, 8) != 0)
+    return bad("not a checkpoint of this library");
+  if (hd.N != h->N || hd.R != h->R) return bad("particle or replica count differs from the handle");
+  if (hd.precision != h->p0.precision) return bad("precision differs from the handle");
+  const int64_t N = h->N;
+  std::vector<susp_params> pr(h->R);
+  std::vector<double> strain(h->R), radii(N), st(15 * N), acc(48 * (size_t)h->R);
+  if (std::fread(pr.data(), sizeof(susp_params), h->R, fc.f) != (size_t)h->R ||
+      std::fread(strain.data(), sizeof(double), h->R, fc.f) != (size_t)h->R ||
+      std::fread(radii.data(), sizeof(double), N, fc.f) != (size_t)N ||
+      std::fread(st.data(), sizeof(double), st.size(), fc.f) != st.size() ||
+      std::fread(acc.data(), sizeof(double), acc.size(), fc.f) != acc.size())
+    return bad("truncated");
+  for (int r = 0; r < h->R; ++r)
+    if (!same_static_params(pr[r], h->pr[r])) return bad("model parameters differ from the handle");
+  if (std::memcmp(radii.data(), h->radii.data(), sizeof(double) * N) != 0)
+    return bad("radii differ from the handle");
+  int64_t np = 0;
+  if (std::fread(&np, sizeof np, 1, fc.f) != 1 || np < 0 || np > 64 * N) return bad("truncated");
+  std::vector<int32_t> ij(2 * std::max<int64_t>(np, 1));
+  std::vector<double> xi(3 * std::max<int64_t>(np, 1));
+  char end[8];
+  if (std::fread(ij.data(), sizeof(int32_t), 2 * np, fc.f) != (size_t)(2 * np) ||
+      std::fread(xi.data(), sizeof(double), 3 * np, fc.f) != (size_t)(3 * np) ||
+      std::fread(end, 1, 8, fc.f) != 8 || std::memcmp(end, kCkEnd, 8) != 0)
+    return bad("truncated");
+  // history rows (tag order): partners of each lower tag
+  std::vector<int> rowlen(N, 0);
+  for (int64_t e = 0; e < np; ++e) {
+    const int32_t i = ij[2 * e], j = ij[2 * e + 1];
+    if (i < 0 || j < 0 || i >= N || j >= N || i == j || h->rep_of[i] != h->rep_of[j])
+      return bad("history pair out of range");
+    if (++rowlen[i] > std::min(h->kmax, 64)) return bad("more touching pairs per sphere than kmax");
+  }
+  // the file is consistent with the handle: from here on the device is used
+  CK(cudaSetDevice(h->dev));
+  int rc = allocate(h);
+  if (rc) return rc;
+  // clock first, so that the state is wrapped in the saved box
+  for (int r = 0; r < h->R; ++r) {
+    Replica& R = h->repl_h[r];
+    if (!(std::fabs(strain[r]) <= R.flip_at)) return bad("strain out of range");
+    R.strain = strain[r];
+    R.tilt = strain[r] * R.L[1];
+    R.rate = pr[r].shear_rate;
+    R.kT = pr[r].kT;
+    R.key0 = (uint32_t)(pr[r].seed & 0xffffffffull);
+    R.key1 = (uint32_t)(pr[r].seed >> 32);
+    h->pr[r].shear_rate = pr[r].shear_rate;
+    h->pr[r].kT = pr[r].kT;
+    h->pr[r].seed = pr[r].seed;
+    h->pr[r].dt = pr[r].dt;
+    refresh_strain_fields(R);
+  }
+  CK(cudaMemcpyAsync(h->A.repl, h->repl_h.data(), sizeof(Replica) * h->R,
+                     cudaMemcpyHostToDevice, h->stream));
+  drop_graphs(h);
+  if (hd.last_dt > 0) h->last_dt = hd.last_dt;
+  rc = set_state_impl(h, st.data(), st.data() + 3 * N, st.data() + 6 * N, cudaMemcpyHostToDevice);
+  if (rc) return rc;
+  long long kk = (long long)hd.k;
+  CK(cudaMemcpyAsync(&h->A.ctl->k, &kk, sizeof kk, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->A.stress_acc, acc.data(), sizeof(double) * acc.size(),
+                     cudaMemcpyHostToDevice, h->stream));
+  Ctl c{};
+  CK(cudaMemcpyAsync(&c, h->A.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const int cur = c.cur;
+  const int64_t Np = h->Npad;
+  const bool mixed = h->p0.precision == SUSP_MIXED;
+  // forces and torques of the last evaluation, in the tag order the state
+  // was just loaded in; the rebuild below permutes them with the state
+  const double* F = st.data() + 9 * N;
+  const double* T = st.data() + 12 * N;
+  if (mixed) {
+    std::vector<float> f4(4 * N), t4(4 * N);
+    for (int64_t p = 0; p < N; ++p)
+      for (int q = 0; q < 4; ++q) {
+        f4[4 * p + q] = q < 3 ? (float)F[3 * p + q] : 0.f;
+        t4[4 * p + q] = q < 3 ? (float)T[3 * p + q] : 0.f;
+      }
+    CK(cudaMemcpy(h->A.frc[cur], f4.data(), sizeof(float) * 4 * N, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->A.trq[cur], t4.data(), sizeof(float) * 4 * N, cudaMemcpyHostToDevice));
+  } else {
+    std::vector<double> col(N);
+    for (int q = 0; q < 3; ++q) {
+      for (int64_t p = 0; p < N; ++p) col[p] = F[3 * p + q];
+      CK(cudaMemcpy(h->A.frc[cur] + q * Np, col.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+      for (int64_t p = 0; p < N; ++p) col[p] = T[3 * p + q];
+      CK(cudaMemcpy(h->A.trq[cur] + q * Np, col.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+    }
+  }
+  // the saved history as the live list: the rebuild carries it into the new
+  // list by (tag_i, tag_j) as it does for any rebuild
+  if (np > 0) {
+    const int m = *std::max_element(rowlen.begin(), rowlen.end());
+    std::vector<int> nbr((size_t)m * N, 0), fill(N, 0);
+    std::vector<double> hv((size_t)3 * m * N, 0.0);
+    std::vector<unsigned long long> cm(N, 0ull);
+    for (int64_t e = 0; e < np; ++e) {
+      const int32_t i = ij[2 * e], j = ij[2 * e + 1];
+      const int sl = fill[i]++;
+      nbr[(size_t)sl * N + i] = j;
+      cm[i] |= 1ull << sl;
+      for (int q = 0; q < 3; ++q) {
+        const double v = xi[3 * e + q];
+        double& slot = hv[((size_t)q * m + sl) * N + i];
+        if (mixed) {
+          const float hi = (float)v;
+          const float lo = (float)(v - (double)hi);
+          float2 f2 = make_float2(hi, lo);
+          std::memcpy(&slot, &f2, sizeof slot);
+        } else {
+          slot = v;
+        }
+      }
+    }
+    const int64_t hs = (int64_t)h->kmax * Np;
+    for (int sl = 0; sl < m; ++sl) {
+      CK(cudaMemcpy(h->A.nbr[cur] + sl * Np, nbr.data() + (size_t)sl * N, sizeof(int) * N,
+                    cudaMemcpyHostToDevice));
+      for (int q = 0; q < 3; ++q)
+        CK(cudaMemcpy(h->A.hist[cur] + q * hs + sl * Np, hv.data() + ((size_t)q * m + sl) * N,
+                      sizeof(double) * N, cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemcpy(h->A.nnb[cur], rowlen.data(), sizeof(int) * N, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->A.cmsk[cur], cm.data(), sizeof(unsigned long long) * N,
+                  cudaMemcpyHostToDevice));
+  }
+  StepArgs s = make_args(h, h->last_dt > 0 ? h->last_dt : h->p0.dt, 0, 0);
+  launch_request_rebuild(h->A, h->stream);
+  launch_rebuild(h->A, h->bm, s, h->stream, mixed);
+  h->steps_done = hd.steps_done;
+  h->forces_valid = hd.forces_valid != 0;
+  return check_errors(h);
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -835,33 +1096,6 @@ int susp_set_allocator(susp_t* h, void* (*alloc)(size_t, void*), void (*release)
   h->ufree = release;
   h->uctx = ctx;
   return SUSP_OK;
-}
-
-static int set_state_impl(susp_t* h, const double* x, const double* U, const double* W,
-                          cudaMemcpyKind kind) {
-  if (!h) return SUSP_EINVAL;
-  h->err.clear();
-  if (!x) return fail(h, SUSP_EINVAL, "positions are required");
-  int rc = allocate(h);
-  if (rc) return rc;
-  CK(cudaSetDevice(h->dev));
-  const size_t bytes = sizeof(double) * 3 * h->N;
-  double* dx = h->d_stage;
-  double* dU = U ? h->d_stage + 3 * h->N : nullptr;
-  double* dW = W ? h->d_stage + 6 * h->N : nullptr;
-  CK(cudaMemcpyAsync(dx, x, bytes, kind, h->stream));
-  if (U) CK(cudaMemcpyAsync(dU, U, bytes, kind, h->stream));
-  if (W) CK(cudaMemcpyAsync(dW, W, bytes, kind, h->stream));
-  // strain/tilt must be current before wrapping
-  rc = sync_replicas(h, h->last_dt);
-  if (rc) return rc;
-  (h->p0.precision == SUSP_MIXED ? launch_load_state_mixed : launch_load_state)(
-      h->A, dx, dU, dW, h->d_radius, h->d_mass, h->d_inertia, h->d_rep_of,
-                    h->stream);
-  launch_request_rebuild(h->A, h->stream);
-  h->have_state = true;
-  h->forces_valid = false;
-  return check_errors(h);
 }
 
 int susp_set_state(susp_t* h, const double* x, const double* U, const double* W) {
@@ -1073,14 +1307,16 @@ int susp_get_info(susp_t* h, double* info) {
 
 int susp_save(susp_t* h, const char* path) {
   if (!h || !path) return SUSP_EINVAL;
+  h->err.clear();
   if (!h->have_state) return fail(h, SUSP_ESTATE, "no state yet");
-  (void)path;
-  return fail(h, SUSP_EINVAL, "checkpointing is not available in this build");
+  CK(cudaSetDevice(h->dev));
+  return save_checkpoint(h, path);
 }
 
 int susp_load(susp_t* h, const char* path) {
   if (!h || !path) return SUSP_EINVAL;
-  return fail(h, SUSP_EINVAL, "checkpointing is not available in this build");
+  h->err.clear();
+  return load_checkpoint(h, path);
 }
 
 }  // extern "C"

@@ -23,6 +23,8 @@
 //     precision, block, global and time sums in double.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "device_common.cuh"
 #include "dfloat.cuh"
 #include "philox.cuh"
@@ -65,42 +67,57 @@ __device__ __forceinline__ Res8<float> resistances_f(float eta, float ai, float 
 
 // Tangential history update in double-float (reading of Sec. II.A): rotate
 // into the current tangent plane keeping the length, add v_t dt, cap at
-// mu kn delta / kt.  xh/xl: hi/lo parts; returns the updated value.
+// mu kn delta / kt.  Over one step the rotation and the increment are small
+// against the stored displacement, so their sum is formed in single
+// precision and added to each double-float component once.
 __device__ __forceinline__ void history_update_df(float* xh, float* xl, const float* n,
                                                   const float* v, float dt, float kt,
                                                   float fmax) {
-  df x0{xh[0], xl[0]}, x1{xh[1], xl[1]}, x2{xh[2], xl[2]};
+  const float nv = n[0] * v[0] + n[1] * v[1] + n[2] * v[2];
+  float c[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) c[q] = (v[q] - n[q] * nv) * dt;
   const float len0sq = xh[0] * xh[0] + xh[1] * xh[1] + xh[2] * xh[2];
   if (len0sq > 0.0f) {
     const float sn = n[0] * xh[0] + n[1] * xh[1] + n[2] * xh[2] +
                      (n[0] * xl[0] + n[1] * xl[1] + n[2] * xl[2]);
     const float q = sn * sn / len0sq;
     if (q < 1.0f) {
-      x0 = df_add_f(x0, -n[0] * sn);
-      x1 = df_add_f(x1, -n[1] * sn);
-      x2 = df_add_f(x2, -n[2] * sn);
-      // restore the length: factor 1/sqrt(1 - q) = 1 + eps
+      // (x - n sn)(1 + eps) - x with 1 + eps = 1/sqrt(1 - q)
       const float eps = q < 1e-3f ? q * (0.5f + 0.375f * q) : rsqrtf(1.0f - q) - 1.0f;
-      x0 = df_add_f(x0, x0.hi * eps);
-      x1 = df_add_f(x1, x1.hi * eps);
-      x2 = df_add_f(x2, x2.hi * eps);
+      const float sc = sn * (1.0f + eps);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) c[k] += xh[k] * eps - n[k] * sc;
     } else {
-      x0 = x1 = x2 = df{0.f, 0.f};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) xh[k] = xl[k] = 0.0f;
     }
   }
-  const float nv = n[0] * v[0] + n[1] * v[1] + n[2] * v[2];
-  x0 = df_add_f(x0, (v[0] - n[0] * nv) * dt);
-  x1 = df_add_f(x1, (v[1] - n[1] * nv) * dt);
-  x2 = df_add_f(x2, (v[2] - n[2] * nv) * dt);
-  const float ft = kt * sqrtf(x0.hi * x0.hi + x1.hi * x1.hi + x2.hi * x2.hi);
+  df x[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) x[k] = df_add_f(df{xh[k], xl[k]}, c[k]);
+  const float ft = kt * sqrtf(x[0].hi * x[0].hi + x[1].hi * x[1].hi + x[2].hi * x[2].hi);
   if (ft > fmax) {
     const float sc = fmax / ft;
-    x0 = df{x0.hi * sc, x0.lo * sc};
-    x1 = df{x1.hi * sc, x1.lo * sc};
-    x2 = df{x2.hi * sc, x2.lo * sc};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) x[k] = df{x[k].hi * sc, x[k].lo * sc};
   }
-  xh[0] = x0.hi; xh[1] = x1.hi; xh[2] = x2.hi;
-  xl[0] = x0.lo; xl[1] = x1.lo; xl[2] = x2.lo;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    xh[k] = x[k].hi;
+    xl[k] = x[k].lo;
+  }
+}
+
+// (qh + ql) - (ph + pl) + (sh + sl) as a double-float (rh, rl): the large
+// parts by two error-free sums, the small parts in single precision.
+__device__ __forceinline__ void df_diff_shift(float qh, float ql, float ph, float pl, float sh,
+                                              float sl, float& rh, float& rl) {
+  float s1, e1, s2, e2;
+  two_sum(qh, -ph, s1, e1);
+  two_sum(s1, sh, s2, e2);
+  const float lo = __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(__fsub_rn(ql, pl), sl));
+  fast_two_sum(s2, lo, rh, rl);
 }
 
 __device__ __forceinline__ void unpack_cell(int v, int& cx, int& cy, int& cz) {
@@ -122,15 +139,23 @@ __device__ __forceinline__ int wrap_dc(int d, int n) {
 template <bool NOISE, bool FRIC, bool SAMPLE>
 __global__ void __launch_bounds__(kBlock, SUSP_PAIR_MINBLOCKS)
 k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
+  constexpr unsigned kFull = 0xffffffffu;
   __shared__ float4 sF[kBlock];
   __shared__ float4 sT[kBlock];
   __shared__ unsigned long long sM[kBlock];
   __shared__ float sW[(kBlock / 32) * kPartialLen];
+  __shared__ float2 sShx[9];   // x shift dcx w_x + dcy tilt/ncy, double-float
   __shared__ int sArrive;
-  if (threadIdx.x == 0) sArrive = 0;
-  __syncthreads();
   const int b = blockIdx.x;
   const int r = bm.rep[b];
+  const Replica& RP = A.repl[r];
+  if (threadIdx.x == 0) sArrive = 0;
+  if (threadIdx.x < 9) {
+    const float fx = (float)((int)threadIdx.x / 3 - 1), fy = (float)((int)threadIdx.x % 3 - 1);
+    const df v = df_add(df{RP.cw_hi[0] * fx, RP.cw_lo[0] * fx}, df{RP.ct_hi * fy, RP.ct_lo * fy});
+    sShx[threadIdx.x] = make_float2(v.hi, v.lo);
+  }
+  __syncthreads();
   const int pb = bm.start[b], pe = bm.end[b];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int p = pb + tid;
@@ -138,12 +163,10 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   const Ctl* ctl = A.ctl;
   const int cur = ctl->cur;
   const long long k = ctl->k;
-  const Replica& RP = A.repl[r];
   const float rate = RP.rate_f, eta = RP.eta_f, kn = RP.kn_f, kt = RP.kt_f, mu = RP.mu_f;
   const float c = RP.noise_cf;
   const float cwx = RP.cwf[0], cwy = RP.cwf[1], cwz = RP.cwf[2], ctilt = RP.ctilt_f;
-  const df cw0{RP.cw_hi[0], RP.cw_lo[0]}, cw1{RP.cw_hi[1], RP.cw_lo[1]},
-      cw2{RP.cw_hi[2], RP.cw_lo[2]}, ct_df{RP.ct_hi, RP.ct_lo};
+  const float cw1h = RP.cw_hi[1], cw1l = RP.cw_lo[1], cw2h = RP.cw_hi[2], cw2l = RP.cw_lo[2];
   const int ncx = RP.nc[0], ncy = RP.nc[1], ncz = RP.nc[2];
   const uint32_t key0 = RP.key0, key1 = RP.key1;
   const int t0 = (int)RP.p0;
@@ -195,10 +218,10 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   int incl = nn;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    const int y = __shfl_up_sync(kFull, incl, o);
     if (lane >= o) incl += y;
   }
-  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  const int total = __shfl_sync(kFull, incl, 31);
   const int excl = incl - nn;
   __syncwarp();
 
@@ -206,22 +229,26 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
 #pragma unroll
   for (int q = 0; q < (SAMPLE ? kPartialLen : 1); ++q) vir[q] = 0.0f;
 
-  // Pairs within the cutoff are queued per warp in shared memory and the
-  // pair physics runs on full 32-lane batches of that queue, so lanes whose
-  // item falls beyond the cutoff do not idle through it.
+  // Pairs within the cutoff are queued per warp in shared memory, touching
+  // pairs (queue 1) apart from the others (queue 0), and the pair physics
+  // runs on full 32-lane batches of one queue: lanes beyond the cutoff do
+  // not idle through it and only touching pairs run the contact branch.
   constexpr int kQ = 64;
-  __shared__ int qQ[kBlock / 32][kQ];
-  __shared__ int qM[kBlock / 32][kQ];        // owner lane | slot << 5 | had contact << 12
-  __shared__ float qG[kBlock / 32][6][kQ];   // r_x, r_y, r_z, d, h, S
-  int qn = 0;
+  __shared__ int qQ[2][kBlock / 32][kQ];
+  __shared__ int qM[2][kBlock / 32][kQ];        // owner lane | slot << 5 | had contact << 12
+  __shared__ float qG[2][kBlock / 32][6][kQ];   // r_x, r_y, r_z, d, h, S
+  int qn0 = 0, qn1 = 0;
 
-  auto pair_physics = [&](int e) {
-    const int q = qQ[warp][e];
-    const int meta = qM[warp][e];
+  // Pair e of queue CT: partner's share by vector reductions, owner's share
+  // returned in v (force, torque) with its contact bit; returns the owner.
+  auto physics = [&](auto CT, int e, float* v, unsigned long long& mbit) -> int {
+    constexpr bool CONTACT = decltype(CT)::value;
+    constexpr int qi = CONTACT ? 1 : 0;
+    const int q = qQ[qi][warp][e];
+    const int meta = qM[qi][warp][e];
     const int o = meta & 31, sl = (meta >> 5) & 127;
-    const bool had = (meta >> 12) & 1;
-    const float rpq[3] = {qG[warp][0][e], qG[warp][1][e], qG[warp][2][e]};
-    const float d = qG[warp][3][e], h = qG[warp][4][e], S = qG[warp][5][e];
+    const float rpq[3] = {qG[qi][warp][0][e], qG[qi][warp][1][e], qG[qi][warp][2][e]};
+    const float d = qG[qi][warp][3][e], h = qG[qi][warp][4][e], S = qG[qi][warp][5][e];
     const float xi = 2.0f * h / S;
     const int po = pb + warp * 32 + o;
     const float4 P = __ldg(PM + 2 * po), Q = __ldg(PM + 2 * q);
@@ -258,17 +285,18 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
       for (int q3 = 0; q3 < 3; ++q3) ou.FL[q3] = ou.FB[q3] = ou.Ti[q3] = ou.Tj[q3] = 0.f;
     }
     float FC[3] = {0.f, 0.f, 0.f}, TCi[3] = {0.f, 0.f, 0.f}, TCj[3] = {0.f, 0.f, 0.f};
-    if (h < 0.0f && s.contact) {
+    mbit = 0ull;
+    if constexpr (CONTACT) {
       const float delta = -h;
       float Ft[3] = {0.f, 0.f, 0.f};
       if (FRIC && mu > 0.0f) {
         float xh[3] = {0.f, 0.f, 0.f}, xl[3] = {0.f, 0.f, 0.f};
         const int64_t hi = (int64_t)sl * Np + po;
-        if (had) {
+        if ((meta >> 12) & 1) {
 #pragma unroll
           for (int q3 = 0; q3 < 3; ++q3) {
-            const float2 v = hist[hi + q3 * hs];
-            xh[q3] = v.x; xl[q3] = v.y;
+            const float2 w = hist[hi + q3 * hs];
+            xh[q3] = w.x; xl[q3] = w.y;
           }
         }
         if (s.advance) {
@@ -276,12 +304,12 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
                                ai * Wi[2] + aj * Wj[2]};
           float wxn[3];
           cross3(ww, n, wxn);
-          const float v[3] = {dU[0] - wxn[0], dU[1] - wxn[1], dU[2] - wxn[2]};
-          history_update_df(xh, xl, n, v, dtf, kt, mu * kn * delta);
+          const float vt[3] = {dU[0] - wxn[0], dU[1] - wxn[1], dU[2] - wxn[2]};
+          history_update_df(xh, xl, n, vt, dtf, kt, mu * kn * delta);
         }
 #pragma unroll
         for (int q3 = 0; q3 < 3; ++q3) hist[hi + q3 * hs] = make_float2(xh[q3], xl[q3]);
-        atomicOr(&sM[warp * 32 + o], 1ull << sl);
+        mbit = 1ull << sl;
         Ft[0] = kt * xh[0]; Ft[1] = kt * xh[1]; Ft[2] = kt * xh[2];
       }
 #pragma unroll
@@ -301,17 +329,10 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
       Ti_[q3] = TCi[q3] + ou.Ti[q3];
       Tj_[q3] = TCj[q3] + ou.Tj[q3];
     }
-    // owner's share (shared memory), partner's share (vector reductions)
-    float4* so = &sF[warp * 32 + o];
-    float4* st = &sT[warp * 32 + o];
     const float* To = p_is_i ? Ti_ : Tj_;
     const float* Tq = p_is_i ? Tj_ : Ti_;
-    atomicAdd(&so->x, sg * Fi[0]);
-    atomicAdd(&so->y, sg * Fi[1]);
-    atomicAdd(&so->z, sg * Fi[2]);
-    atomicAdd(&st->x, To[0]);
-    atomicAdd(&st->y, To[1]);
-    atomicAdd(&st->z, To[2]);
+    v[0] = sg * Fi[0]; v[1] = sg * Fi[1]; v[2] = sg * Fi[2];
+    v[3] = To[0]; v[4] = To[1]; v[5] = To[2];
     red_add_v4(F4 + q, -sg * Fi[0], -sg * Fi[1], -sg * Fi[2], 0.f);
     red_add_v4(T4 + q, Tq[0], Tq[1], Tq[2], 0.f);
     if (SAMPLE) {
@@ -319,11 +340,52 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
       for (int al = 0; al < 3; ++al)
 #pragma unroll
         for (int be = 0; be < 3; ++be) {
-          vir[3 * al + be] += FC[al] * rr[be];
+          if constexpr (CONTACT) vir[3 * al + be] += FC[al] * rr[be];
           vir[9 + 3 * al + be] += ou.FL[al] * rr[be];
           vir[18 + 3 * al + be] += ou.FB[al] * rr[be];
         }
     }
+    return o;
+  };
+
+  // One batch of `count` (warp-uniform, 1..32) consecutive entries of queue
+  // CT.  Queue entries are in row order, so the owners along a batch are
+  // non-decreasing: the owner's shares are summed over each run of equal
+  // owners by shuffles, and the run's first lane adds the sums to the
+  // owner's shared-memory accumulators (one writer per owner per batch).
+  auto batch = [&](auto CT, int first, int count) {
+    constexpr bool CONTACT = decltype(CT)::value;
+    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    unsigned long long mb = 0ull;
+    int own = 32;  // idle lanes: past every owner
+    if (lane < count) own = physics(CT, first + lane, v, mb);
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int oo = __shfl_down_sync(kFull, own, off);
+      const bool same = lane + off < 32 && oo == own && own < 32;
+      if (!__any_sync(kFull, same)) break;  // every run is at most off long
+#pragma unroll
+      for (int cc = 0; cc < 6; ++cc) {
+        const float x = __shfl_down_sync(kFull, v[cc], off);
+        if (same) v[cc] += x;
+      }
+      if (FRIC && CONTACT) {
+        const unsigned long long x = __shfl_down_sync(kFull, mb, off);
+        if (same) mb |= x;
+      }
+    }
+    const int prev = __shfl_up_sync(kFull, own, 1);
+    if (own < 32 && (lane == 0 || prev != own)) {
+      float4* so = &sF[warp * 32 + own];
+      float4* st = &sT[warp * 32 + own];
+      float4 f = *so, t = *st;
+      f.x += v[0]; f.y += v[1]; f.z += v[2];
+      t.x += v[3]; t.y += v[4]; t.z += v[5];
+      *so = f;
+      *st = t;
+      if (FRIC && CONTACT) sM[warp * 32 + own] |= mb;
+    }
+    __syncwarp();
   };
 
   for (int base = 0; base < total; base += 32) {
@@ -332,12 +394,12 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
     int o = 0;
 #pragma unroll
     for (int step = 16; step > 0; step >>= 1) {
-      const int v = __shfl_sync(0xffffffffu, incl, o + step - 1);
+      const int v = __shfl_sync(kFull, incl, o + step - 1);
       if (v <= t) o += step;
     }
-    const int oexcl = __shfl_sync(0xffffffffu, excl, o);
-    const unsigned long long ocm = FRIC ? __shfl_sync(0xffffffffu, cm_own, o) : 0ull;
-    bool keep = false;
+    const int oexcl = __shfl_sync(kFull, excl, o);
+    const unsigned long long ocm = FRIC ? __shfl_sync(kFull, cm_own, o) : 0ull;
+    bool keep = false, touch = false;
     int q = 0, sl = 0;
     float gq[6];
     if (t < total) {
@@ -358,43 +420,73 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
       // beyond the lubrication cutoff (with a margin for single-precision
       // rounding; the exact test follows): no force, no contact
       if (d2f <= rc * rc * 1.00001f) {
-        // separation and gap in double-float: h = (d^2 - S^2) / (d + S)
+        // separation in double-float from the cell-relative offsets, then
+        // d^2 - S^2 with the cancelling squares summed error-free, and the
+        // gap h = (d^2 - S^2) / (d + S)
         const float4 Pl = __ldg(PM + 2 * po + 1), Ql = __ldg(PM + 2 * q + 1);
-        const df rx = df_add(df_diff(Q.x, Ql.x, P.x, Pl.x),
-                             df_add(df_mul_f(cw0, (float)dcx), df_mul_f(ct_df, (float)dcy)));
-        const df ry = df_add(df_diff(Q.y, Ql.y, P.y, Pl.y), df_mul_f(cw1, (float)dcy));
-        const df rz = df_add(df_diff(Q.z, Ql.z, P.z, Pl.z), df_mul_f(cw2, (float)dcz));
-        const df dd = df_add(df_add(df_mul(rx, rx), df_mul(ry, ry)), df_mul(rz, rz));
-        const df Sd = df_add(df{P.w, Pl.w}, df{Q.w, Ql.w});
-        const float S = Sd.hi;
-        const float d = sqrtf(dd.hi);
-        const float h = df_to_f(df_sub(dd, df_mul(Sd, Sd))) / (d + S);
-        if (2.0f * h / S <= xi_max) {
+        const float2 shx = sShx[(dcx + 1) * 3 + (dcy + 1)];
+        const float fy = (float)dcy, fz = (float)dcz;
+        float rh[3], rl[3];
+        df_diff_shift(Q.x, Ql.x, P.x, Pl.x, shx.x, shx.y, rh[0], rl[0]);
+        df_diff_shift(Q.y, Ql.y, P.y, Pl.y, cw1h * fy, cw1l * fy, rh[1], rl[1]);
+        df_diff_shift(Q.z, Ql.z, P.z, Pl.z, cw2h * fz, cw2l * fz, rh[2], rl[2]);
+        float Sh, Sl;
+        {
+          float s0, e0;
+          two_sum(P.w, Q.w, s0, e0);
+          fast_two_sum(s0, __fadd_rn(e0, __fadd_rn(Pl.w, Ql.w)), Sh, Sl);
+        }
+        float pk[3], ek[3];
+#pragma unroll
+        for (int k3 = 0; k3 < 3; ++k3) {
+          pk[k3] = __fmul_rn(rh[k3], rh[k3]);
+          ek[k3] = __fmaf_rn(rh[k3], rh[k3], -pk[k3]);
+        }
+        const float pS = __fmul_rn(Sh, Sh);
+        const float eS = __fmaf_rn(Sh, Sh, -pS);
+        float t1, u1, t2, u2, t3, u3;
+        two_sum(pk[0], pk[1], t1, u1);
+        two_sum(t1, pk[2], t2, u2);
+        two_sum(t2, -pS, t3, u3);
+        const float small = ((u1 + u2) + u3) + ((ek[0] + ek[1]) + (ek[2] - eS)) +
+                            2.0f * ((rh[0] * rl[0] + rh[1] * rl[1]) + (rh[2] * rl[2] - Sh * Sl));
+        const float D = __fadd_rn(t3, small);
+        const float d = sqrtf(t2);
+        const float h = D / (d + Sh);
+        if (2.0f * h / Sh <= xi_max) {
           keep = true;
-          gq[0] = df_to_f(rx); gq[1] = df_to_f(ry); gq[2] = df_to_f(rz);
-          gq[3] = d; gq[4] = h; gq[5] = S;
+          touch = s.contact && h < 0.0f;
+          gq[0] = rh[0]; gq[1] = rh[1]; gq[2] = rh[2];
+          gq[3] = d; gq[4] = h; gq[5] = Sh;
         }
       }
     }
-    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    const unsigned m0 = __ballot_sync(kFull, keep && !touch);
+    const unsigned m1 = __ballot_sync(kFull, touch);
     if (keep) {
-      const int e = qn + __popc(m & ((1u << lane) - 1u));
-      qQ[warp][e] = q;
-      qM[warp][e] = o | (sl << 5) | ((FRIC && ((ocm >> sl) & 1ull)) ? (1 << 12) : 0);
+      const unsigned below = (1u << lane) - 1u;
+      const int qi = touch ? 1 : 0;
+      const int e = touch ? qn1 + __popc(m1 & below) : qn0 + __popc(m0 & below);
+      qQ[qi][warp][e] = q;
+      qM[qi][warp][e] = o | (sl << 5) | ((FRIC && ((ocm >> sl) & 1ull)) ? (1 << 12) : 0);
 #pragma unroll
-      for (int c6 = 0; c6 < 6; ++c6) qG[warp][c6][e] = gq[c6];
+      for (int c6 = 0; c6 < 6; ++c6) qG[qi][warp][c6][e] = gq[c6];
     }
-    qn += __popc(m);
+    qn0 += __popc(m0);
+    qn1 += __popc(m1);
     __syncwarp();
-    if (qn >= 32) {
-      pair_physics(qn - 32 + lane);
-      qn -= 32;
-      __syncwarp();
+    if (qn0 >= 32) {
+      batch(std::false_type{}, qn0 - 32, 32);
+      qn0 -= 32;
+    }
+    if (qn1 >= 32) {
+      batch(std::true_type{}, qn1 - 32, 32);
+      qn1 -= 32;
     }
   }
-  if (lane < qn) pair_physics(lane);
-  // the warp's own accumulators are complete once its lanes are done
-  __syncwarp();
+  if (qn0 > 0) batch(std::false_type{}, 0, qn0);
+  if (qn1 > 0) batch(std::true_type{}, 0, qn1);
+  // the warp's own accumulators are complete once its batches are done
   if (active) {
     const float4 f = sF[tid], t = sT[tid];
     red_add_v4(F4 + p, f.x, f.y, f.z, 0.f);
@@ -410,13 +502,13 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
     for (int cc = 0; cc < kPartialLen; ++cc) {
       float x = vir[cc];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
       if (lane == 0) sW[warp * kPartialLen + cc] = x;
     }
     __threadfence_block();
     int arrived = 0;
     if (lane == 0) arrived = atomicAdd(&sArrive, 1);
-    arrived = __shfl_sync(0xffffffffu, arrived, 0);
+    arrived = __shfl_sync(kFull, arrived, 0);
     if (arrived == kBlock / 32 - 1) {
       __threadfence_block();
       if (lane < kPartialLen) {

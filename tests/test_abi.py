@@ -51,3 +51,4 @@ def test_create_without_gpu_fails_cleanly():
         assert e.code == s.SUSP_ENODEV
     else:
         raise AssertionError("expected SUSP_ENODEV without a GPU")
+
