@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true",
                     help="skip the FP64-path comparison line")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads (FP64 10k, 256 replicas, 8M) and the "
+                         "mixed-vs-FP64 accuracy run")
     return ap.parse_args()
 
 
@@ -290,6 +293,30 @@ def run_ours(args, rank, world, local_rank, dist):
                 "speedup_of_mixed": round(value / (world * N * n64 / (ms64 / 1e3)), 2)}
         s64.close()
 
+    legs = {}
+    if not args.no_configs and world == 1:
+        x0, U0, W0 = sysm.state()
+        i0 = sysm.info()
+        sysm.close()
+
+        def leg(fn):
+            # a library error in one extra workload is reported, not fatal
+            try:
+                return fn()
+            except susp.SuspError as e:
+                return {"error": str(e)}
+
+        legs["mixed_vs_fp64"] = leg(lambda: mixed_vs_fp64(
+            susp, w, x0, U0, W0, int(i0["k"]), float(i0["strain"]), stream))
+        legs["configs"] = {
+            "bidisperse-10k-phi0.56-pe10-mu1 (fp64)": leg(lambda: run_single(
+                susp, workloads.named("bidisperse-10k-phi0.56"), "fp64", stream, 100, 5)),
+            "batched-256-replicas (mixed)": leg(lambda: run_batched(susp, stream)),
+            "polydisperse-8M-phi0.60-pe100-mu1 (mixed)": leg(lambda: run_single(
+                susp, workloads.named("polydisperse-8M-phi0.60-pe100-mu1"), "mixed", stream,
+                100, 3)),
+        }
+
     launches = int(info1["launches"] - info0["launches"])
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": METRIC,
@@ -312,8 +339,122 @@ def run_ours(args, rank, world, local_rank, dist):
     }
     if fp64:
         out["fp64_path"] = fp64
+    out.update(legs)
     if clk:
         out["clocks"] = clk
+    return out
+
+
+def _timed(stream, fn):
+    """Device milliseconds of fn() on `stream` (CUDA events, synchronised)."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def _system(susp, w, precision, stream):
+    p = w.params
+    s = susp.System(w.radii, w.box, precision=precision, eta=p["eta"], rho=p["rho"],
+                    kn=p["kn"], kt=p["kt"], mu=p["mu"], skin=p["skin"],
+                    shear_rate=p["shear_rate"], kT=p["kT"], seed=p["seed"], dt=p["dt"])
+    s.set_stream(stream.cuda_stream)
+    s.set_state(w.x, w.U, w.W)
+    return s
+
+
+def run_single(susp, w, precision, stream, inner, steps, warmup=1):
+    """particle-steps/s of one handle on workload w."""
+    p = w.params
+    s = _system(susp, w, precision, stream)
+    for _ in range(warmup):
+        s.step(inner, p["shear_rate"], p["kT"], p["dt"], p["seed"])
+
+    def run():
+        for _ in range(steps):
+            s.step(inner, p["shear_rate"], p["kT"], p["dt"], p["seed"])
+    ms = _timed(stream, run)
+    eta = s.stress()["eta_r"]
+    s.close()
+    return {"value": round(w.N * inner * steps / (ms / 1e3), 1), "N": w.N,
+            "precision": precision, "timesteps": inner * steps,
+            "ms_per_timestep": round(ms / (inner * steps), 4), "eta_r": round(float(eta), 4)}
+
+
+def run_batched(susp, stream, inner=100, steps=3):
+    """particle-steps/s of the 256-replica ensemble (N ~ U[500, 20000],
+    phi ~ U[0.45, 0.60], Pe log-uniform in [0.1, 1000], mu in {0, 0.5, 1})
+    stepped by one batch handle, mixed precision."""
+    import numpy as np
+    import workloads
+    table = workloads.replica_table()
+    t0 = time.perf_counter()
+    ws = workloads.make_replicas(table, tol=1e-2, processes=max(1, (os.cpu_count() or 2) - 1))
+    gen_s = time.perf_counter() - t0
+    kw = []
+    for w in ws:
+        p = w.params
+        kw.append(dict(precision="mixed", eta=p["eta"], rho=p["rho"], kn=p["kn"], kt=p["kt"],
+                       mu=p["mu"], skin=p["skin"], shear_rate=p["shear_rate"], kT=p["kT"],
+                       seed=p["seed"], dt=p["dt"]))
+    sizes = [w.N for w in ws]
+    b = susp.System.batch(sizes, np.concatenate([w.radii for w in ws]),
+                          np.stack([w.box for w in ws]), kw)
+    b.set_stream(stream.cuda_stream)
+    b.set_state(np.concatenate([w.x for w in ws]), np.concatenate([w.U for w in ws]),
+                np.concatenate([w.W for w in ws]))
+    dt = ws[0].params["dt"]
+    b.step_batch(inner, dt)
+
+    def run():
+        for _ in range(steps):
+            b.step_batch(inner, dt)
+    ms = _timed(stream, run)
+    total = int(sum(sizes))
+    etas = [b.stress(r)["eta_r"] for r in range(len(ws))]
+    b.close()
+    return {"value": round(total * inner * steps / (ms / 1e3), 1), "replicas": len(ws),
+            "particles": total, "precision": "mixed", "timesteps": inner * steps,
+            "ms_per_timestep": round(ms / (inner * steps), 4),
+            "finite_eta_r": bool(all(math.isfinite(e) for e in etas)),
+            "packing_tol": 1e-2, "generation_s": round(gen_s, 1)}
+
+
+def mixed_vs_fp64(susp, w, x, U, Wv, k, strain, stream, steps=500):
+    """Accuracy of the mixed path against the FP64 path from one state:
+    one evaluation (forces, torques, pair stresses, relative to the largest
+    entry) and the relative viscosity averaged over `steps` timesteps run
+    from that state with the same noise."""
+    import numpy as np
+    p = w.params
+    out = {"N": w.N, "steps": steps}
+    res = {}
+    for prec in ("mixed", "fp64"):
+        s = _system(susp, w, prec, stream)
+        s.set_state(x, U, Wv)
+        s.set_clock(k, strain)
+        s.evaluate()
+        F, T = s.forces()
+        sig = s.stress()
+        s.step(steps, p["shear_rate"], p["kT"], p["dt"], p["seed"])
+        run = s.stress()
+        res[prec] = (F, T, sig, run)
+        s.close()
+    Fm, Tm, sm, rm = res["mixed"]
+    Fd, Td, sd, rd = res["fp64"]
+    out["force_err"] = float(np.abs(Fm - Fd).max() / np.abs(Fd).max())
+    out["torque_err"] = float(np.abs(Tm - Td).max() / np.abs(Td).max())
+    for key in ("contact", "lubrication", "brownian"):
+        out[f"{key}_stress_err"] = float(np.abs(sm[key] - sd[key]).max() / np.abs(sd[key]).max())
+    out["eta_r_mixed"] = round(float(rm["eta_r"]), 6)
+    out["eta_r_fp64"] = round(float(rd["eta_r"]), 6)
+    out["eta_r_rel_err"] = float(abs(rm["eta_r"] / rd["eta_r"] - 1.0))
+    out["N1_rel_err"] = float(abs(rm["N1"] - rd["N1"]) / max(abs(rd["N1"]), 1e-300))
     return out
 
 

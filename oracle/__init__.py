@@ -36,7 +36,7 @@ def build(force: bool = False) -> str:
 
 
 class Params(C.Structure):
-    """Mirror of ``o_params`` in oracle.c (doubles, then int64s)."""
+    """Mirror of ``o_params`` in oracle.c."""
     _fields_ = [
         ("eta", C.c_double), ("rho", C.c_double), ("kn", C.c_double),
         ("kt", C.c_double), ("mu", C.c_double), ("xi_min", C.c_double),
@@ -46,13 +46,16 @@ class Params(C.Structure):
         ("seed", C.c_int64), ("noise", C.c_int64), ("lubrication", C.c_int64),
         ("onebody", C.c_int64), ("contact", C.c_int64), ("freeze", C.c_int64),
         ("rebuild_every_step", C.c_int64),
+        ("rep_A", C.c_double), ("rep_cut", C.c_double), ("shell", C.c_double),
+        ("structural", C.c_int64),
     ]
 
 
 DEFAULTS = dict(eta=1.0, rho=1.0, kn=1e4, kt=0.0, mu=0.0, xi_min=1e-3,
                 xi_max=0.05, skin=0.3, shear_rate=1.0, kT=0.0, dt=1e-4,
                 torque_sign=-1.0, seed=0, noise=1, lubrication=1, onebody=1,
-                contact=1, freeze=0, rebuild_every_step=0)
+                contact=1, freeze=0, rebuild_every_step=0, rep_A=0.0, rep_cut=10.0,
+                shell=0.05, structural=0)
 
 
 def make_params(**kw) -> Params:
@@ -110,6 +113,10 @@ def lib():
                                        C.c_double]
         L.o_drag_stress_xy.restype = C.c_double
         L.o_timescales.argtypes = [C.c_double] * 6 + [_D]
+        L.o_autocorr.argtypes = [_D, C.c_int64, C.c_int64, _D]
+        L.o_green_kubo.argtypes = [_D, C.c_int64, C.c_int64, C.c_double, C.c_double,
+                                   C.c_double, _D, _D]
+        L.o_gk_fit.argtypes = [_D, C.c_int64, C.c_double, C.c_int64, _D]
         _lib = L
     return _lib
 
@@ -181,6 +188,25 @@ def timescales(a, rho, kn, eta, kT, rate) -> np.ndarray:
     return out
 
 
+def green_kubo(series, max_lag: int, dt: float, V: float, kT: float):
+    """Autocorrelation C(tau) of a stress series and the running Green-Kubo
+    integral eta(t) = V/kT int_0^t C (Eq. 33, trapezoid rule)."""
+    x = _f64(series)
+    C_, eta = np.zeros(max_lag), np.zeros(max_lag)
+    lib().o_green_kubo(_dp(x), len(x), int(max_lag), float(dt), float(V), float(kT),
+                       _dp(C_), _dp(eta))
+    return C_, eta
+
+
+def gk_fit(eta, dt: float, grid: int = 400):
+    """(eta_phi, tau_phi) of eta(t) ~ eta_phi (1 - exp(-t/tau_phi)) by least
+    squares on a log grid of tau (Sec. III.D)."""
+    e = _f64(eta)
+    out = np.zeros(2)
+    lib().o_gk_fit(_dp(e), len(e), float(dt), int(grid), _dp(out))
+    return float(out[0]), float(out[1])
+
+
 # ---------------------------------------------------------------------------
 # a simulated system
 # ---------------------------------------------------------------------------
@@ -243,21 +269,21 @@ class System:
         lib().o_get_forces(self._h, _dp(F), _dp(T))
         return F, T
 
+    _KEYS = ("contact", "lubrication", "brownian", "repulsion", "structural",
+             "kinetic", "kinetic_rot")
+
     def stress(self):
         """Last evaluation: dict of 3x3 tensors (contact, lubrication,
-        brownian) and kinetic tensors of the last full-step velocities."""
-        out = np.zeros(45)
+        brownian pair, repulsion, structural Brownian) and the kinetic
+        tensors of the last full-step velocities."""
+        out = np.zeros(63)
         lib().o_get_stress(self._h, _dp(out))
-        t = out.reshape(5, 3, 3)
-        return dict(contact=t[0], lubrication=t[1], brownian=t[2],
-                    kinetic=t[3], kinetic_rot=t[4])
+        return dict(zip(self._KEYS, out.reshape(7, 3, 3)))
 
     def take_stress_sums(self):
-        out = np.zeros(45)
+        out = np.zeros(63)
         n = lib().o_take_stress_sums(self._h, _dp(out))
-        t = out.reshape(5, 3, 3)
-        return n, dict(contact=t[0], lubrication=t[1], brownian=t[2],
-                       kinetic=t[3], kinetic_rot=t[4])
+        return n, dict(zip(self._KEYS, out.reshape(7, 3, 3)))
 
     def info(self):
         out = np.zeros(8)

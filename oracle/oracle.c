@@ -86,6 +86,10 @@ typedef struct {
   int64_t contact;   /* 1: contact forces on */
   int64_t freeze;    /* 1: positions are not advanced (test mode) */
   int64_t rebuild_every_step; /* 1: rebuild the Verlet list at every step */
+  double rep_A;      /* repulsion force scale A of Eq. 34 (0: off) */
+  double rep_cut;    /* repulsion acts for h <= rep_cut kappa, kappa = 0.01 (a_i + a_j) */
+  double shell;      /* structural Brownian shell Delta / a_i of Eq. 26 */
+  int64_t structural;/* 1: structural Brownian stress (Eq. 26) on */
 } o_params;
 
 typedef struct {
@@ -111,10 +115,11 @@ typedef struct {
   double t_since_build;
   int64_t nbuilds;
   int32_t forces_valid;
-  /* per-evaluation stresses: [0]=contact [1]=lubrication [2]=Brownian pair */
-  double sigma[3][9];
+  /* per-evaluation stresses: [0]=contact [1]=lubrication [2]=Brownian pair
+   * [3]=repulsion [4]=structural Brownian (Eq. 26) */
+  double sigma[5][9];
   double kin[2][9];  /* kinetic tensors (translational, rotational) of full-step velocities */
-  double sum_sigma[3][9];
+  double sum_sigma[5][9];
   double sum_kin[2][9];
   int64_t nsamples;
   /* diagnostics of the last evaluation */
@@ -337,10 +342,27 @@ static void wrap_particle(o_sys* s, int i) {
 
 /* ------------------------------------------------------------------ */
 /* Verlet list: brute force O(N^2), pairs with d^2 < r_list^2,          */
-/* r_list = (a_i + a_j)(1 + xi_max/2) + skin; history carried by (i,j). */
+/* r_list = r_int + skin; history carried by (i,j).  r_int is the       */
+/* largest centre distance at which a pair interacts: the lubrication   */
+/* cutoff (a_i + a_j)(1 + xi_max/2), with repulsion on also             */
+/* (a_i + a_j)(1 + 0.01 rep_cut), with the structural stress on also    */
+/* a_i + a_j + shell max(a_i, a_j).                                      */
 /* ------------------------------------------------------------------ */
+static double interaction_cut(const o_sys* s, double ai, double aj) {
+  double r = (ai + aj) * (1.0 + 0.5 * s->p.xi_max);
+  if (s->p.rep_A > 0.0) {
+    double rr = (ai + aj) * (1.0 + 0.01 * s->p.rep_cut);
+    if (rr > r) r = rr;
+  }
+  if (s->p.structural) {
+    double rs = (ai + aj) + s->p.shell * (ai > aj ? ai : aj);
+    if (rs > r) r = rs;
+  }
+  return r;
+}
+
 static double list_cut(const o_sys* s, double ai, double aj) {
-  return (ai + aj) * (1.0 + 0.5 * s->p.xi_max) + s->p.skin;
+  return interaction_cut(s, ai, aj) + s->p.skin;
 }
 
 static int entry_cmp(const o_entry* e, int32_t i, int32_t j) {
@@ -449,12 +471,42 @@ static void evaluate(o_sys* s, int advance) {
     double S = s->a[i] + s->a[j];
     double h = d - S;               /* surface gap */
     double xi = 2.0 * h / S;        /* dimensionless gap, Sec. II.B */
-    if (xi > p->xi_max) {           /* outside lubrication range: no contact */
+    double kappa = 0.01 * S;        /* repulsion length, Eq. 34 */
+    int lub = xi <= p->xi_max;
+    int rep = p->rep_A > 0.0 && h <= p->rep_cut * kappa;
+    int shell_i = p->structural && h <= p->shell * s->a[i];
+    int shell_j = p->structural && h <= p->shell * s->a[j];
+    if (!lub) {                     /* outside lubrication range: no contact */
       en->in_contact = 0;
       en->hist[0] = en->hist[1] = en->hist[2] = 0.0;
+    }
+    if (!lub && !rep && !shell_i && !shell_j) continue;
+    double n[3] = {r[0] / d, r[1] / d, r[2] / d};
+    if (shell_i || shell_j) {
+      /* Eq. 26: each sphere i counts the neighbours j in its shell
+       * h <= Delta = shell a_i with weight a_i / Delta = 1 / shell; the pair
+       * enters once from each side whose shell holds it */
+      double w = (shell_i ? 1.0 / p->shell : 0.0) + (shell_j ? 1.0 / p->shell : 0.0);
+      for (int al = 0; al < 3; ++al)
+        for (int be = 0; be < 3; ++be)
+          s->sigma[4][3 * al + be] += -p->kT * w * n[al] * n[be];
+    }
+    double FR[3] = {0, 0, 0};
+    if (rep) {
+      /* Eq. 34 read as the force on j, (A/kappa) exp((S - d)/kappa) n_ij:
+       * on i it is the opposite */
+      double f = p->rep_A / kappa * exp(-h / kappa);
+      for (int q = 0; q < 3; ++q) FR[q] = -f * n[q];
+      for (int al = 0; al < 3; ++al)
+        for (int be = 0; be < 3; ++be) s->sigma[3][3 * al + be] += FR[al] * r[be];
+    }
+    if (!lub) {
+      for (int q = 0; q < 3; ++q) {
+        s->F[3 * i + q] += FR[q];
+        s->F[3 * j + q] -= FR[q];
+      }
       continue;
     }
-    double n[3] = {r[0] / d, r[1] / d, r[2] / d};
     const double* Ui = s->U + 3 * i;
     const double* Uj = s->U + 3 * j;
     const double* Wi = s->W + 3 * i;
@@ -535,7 +587,7 @@ static void evaluate(o_sys* s, int advance) {
       en->hist[0] = en->hist[1] = en->hist[2] = 0.0;
     }
     for (int q = 0; q < 3; ++q) {
-      double Fi = FC[q] + FL[q] + FB[q];
+      double Fi = FC[q] + FL[q] + FB[q] + FR[q];
       s->F[3 * i + q] += Fi;
       s->F[3 * j + q] -= Fi;
       s->T[3 * i + q] += TCi[q] + TLi[q] + TBi[q];
@@ -548,7 +600,7 @@ static void evaluate(o_sys* s, int advance) {
         s->sigma[2][3 * al + be] += FB[al] * r[be];
       }
   }
-  for (int comp = 0; comp < 3; ++comp)
+  for (int comp = 0; comp < 5; ++comp)
     for (int q = 0; q < 9; ++q) s->sigma[comp][q] = s->sigma[comp][q] / V;
   s->forces_valid = 1;
 }
@@ -639,7 +691,7 @@ int o_build(o_sys* s) { return build_list(s); }
 static double max_list_cut(const o_sys* s) {
   double amax = 0.0;
   for (int32_t i = 0; i < s->N; ++i) if (s->a[i] > amax) amax = s->a[i];
-  return (amax + amax) * (1.0 + 0.5 * s->p.xi_max);
+  return interaction_cut(s, amax, amax);
 }
 
 /* Advance n Velocity-Verlet steps. */
@@ -699,7 +751,7 @@ int o_step(o_sys* s, int64_t nsteps) {
         s->W[3 * i + q] = s->W[3 * i + q] + hdt * s->T[3 * i + q] / s->I[i];
       }
     kinetic(s);
-    for (int comp = 0; comp < 3; ++comp)
+    for (int comp = 0; comp < 5; ++comp)
       for (int q = 0; q < 9; ++q) s->sum_sigma[comp][q] += s->sigma[comp][q];
     for (int comp = 0; comp < 2; ++comp)
       for (int q = 0; q < 9; ++q) s->sum_kin[comp][q] += s->kin[comp][q];
@@ -721,17 +773,18 @@ void o_get_forces(const o_sys* s, double* F, double* T) {
   if (T) memcpy(T, s->T, sizeof(double) * n3);
 }
 
-/* out: [3][9] pair stresses of the last evaluation, then [2][9] kinetic */
+/* out: [5][9] pair stresses of the last evaluation (contact, lubrication,
+ * Brownian pair, repulsion, structural Brownian), then [2][9] kinetic */
 void o_get_stress(const o_sys* s, double* out) {
   memcpy(out, s->sigma, sizeof(s->sigma));
-  memcpy(out + 27, s->kin, sizeof(s->kin));
+  memcpy(out + 45, s->kin, sizeof(s->kin));
 }
 
-/* out: time sums since the last reset: [3][9] pair stresses, [2][9] kinetic;
+/* out: time sums since the last reset: [5][9] pair stresses, [2][9] kinetic;
  * returns the number of samples and resets. */
 int64_t o_take_stress_sums(o_sys* s, double* out) {
   memcpy(out, s->sum_sigma, sizeof(s->sum_sigma));
-  memcpy(out + 27, s->sum_kin, sizeof(s->sum_kin));
+  memcpy(out + 45, s->sum_kin, sizeof(s->sum_kin));
   int64_t n = s->nsamples;
   memset(s->sum_sigma, 0, sizeof(s->sum_sigma));
   memset(s->sum_kin, 0, sizeof(s->sum_kin));
@@ -793,4 +846,56 @@ void o_timescales(double a, double rho, double kn, double eta, double kT,
   out[2] = eta * a * a * a / kT;                /* tau_B */
   out[3] = 1.0 / rate;                          /* tau_S */
   out[4] = 6.0 * O_PI * eta * a * a * a * rate / kT; /* Pe = 6 pi tau_B / tau_S */
+}
+
+/* ------------------------------------------------------------------ */
+/* Green-Kubo Brownian viscosity, Eq. 33 (Sec. III.D)                   */
+/* ------------------------------------------------------------------ */
+/* C(tau) = <x(t + tau) x(t)> for tau = 0 .. max_lag - 1 sample steps,   */
+/* the average over the n - tau available origins.                      */
+void o_autocorr(const double* x, int64_t n, int64_t max_lag, double* C) {
+  for (int64_t tau = 0; tau < max_lag; ++tau) {
+    double acc = 0.0;
+    int64_t cnt = n - tau;
+    for (int64_t t = 0; t < cnt; ++t) acc = acc + x[t + tau] * x[t];
+    C[tau] = cnt > 0 ? acc / (double)cnt : 0.0;
+  }
+}
+
+/* eta(t_m) = V / kT * integral_0^{t_m} C dt' with the trapezoid rule on
+ * the sample spacing dt: eta[0] = 0, eta[m] = eta[m-1] + dt (C[m-1] + C[m]) / 2. */
+void o_green_kubo(const double* x, int64_t n, int64_t max_lag, double dt, double V,
+                  double kT, double* C, double* eta) {
+  o_autocorr(x, n, max_lag, C);
+  double pref = V / kT;
+  if (max_lag > 0) eta[0] = 0.0;
+  for (int64_t m = 1; m < max_lag; ++m)
+    eta[m] = eta[m - 1] + pref * dt * 0.5 * (C[m - 1] + C[m]);
+}
+
+/* Fit eta(t) ~ eta_phi (1 - exp(-t / tau_phi)) (Sec. III.D): for each tau
+ * on the grid tau_g = dt * (10 M)^(g / (G - 1)), g = 0 .. G-1, the least-
+ * squares eta_phi(tau) = sum eta f / sum f^2 with f = 1 - exp(-t_m / tau);
+ * the grid point of smallest residual wins.  out = {eta_phi, tau_phi}. */
+void o_gk_fit(const double* eta, int64_t M, double dt, int64_t G, double* out) {
+  double best = -1.0, best_eta = 0.0, best_tau = 0.0;
+  for (int64_t g = 0; g < G; ++g) {
+    double tau = dt * pow(10.0 * (double)M, (double)g / (double)(G - 1));
+    double sff = 0.0, sef = 0.0;
+    for (int64_t m = 0; m < M; ++m) {
+      double f = 1.0 - exp(-(double)m * dt / tau);
+      sff = sff + f * f;
+      sef = sef + eta[m] * f;
+    }
+    double e = sff > 0.0 ? sef / sff : 0.0;
+    double res = 0.0;
+    for (int64_t m = 0; m < M; ++m) {
+      double f = 1.0 - exp(-(double)m * dt / tau);
+      double d = eta[m] - e * f;
+      res = res + d * d;
+    }
+    if (best < 0.0 || res < best) { best = res; best_eta = e; best_tau = tau; }
+  }
+  out[0] = best_eta;
+  out[1] = best_tau;
 }

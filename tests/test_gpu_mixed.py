@@ -121,3 +121,30 @@ def test_equipartition_at_rest(susp, precision):
     Tr = np.trace(s["kinetic_rot"]) * V / (3 * w.N)
     assert Tt == pytest.approx(kT, rel=0.015)
     assert Tr == pytest.approx(kT, rel=0.015)
+
+
+def test_mixed_viscosity_within_one_percent_of_fp64(susp):
+    """The accuracy bar of the mixed path: the relative viscosity and normal
+    stress differences of a sheared, frictional, Brownian suspension, averaged
+    over 2,000 steps from the same state with the same noise, within 1% of the
+    FP64 path.  Over 0.2 strain units the two trajectories stay close, so the
+    measured difference is far below the bar (it is printed)."""
+    w = workloads.make(10_000, 0.56, 100.0, 1.0, pack_seed=81, dyn_seed=82)
+    p = w.params
+    res = {}
+    for prec in ("fp64", "mixed"):
+        g = _sys(susp, w, prec)
+        g.set_state(w.x, w.U, w.W)
+        g.step(500, p["shear_rate"], p["kT"], p["dt"], p["seed"])
+        g.stress()                      # discard the start-up
+        g.step(2000, p["shear_rate"], p["kT"], p["dt"], p["seed"])
+        res[prec] = g.stress()
+    e64, e32 = res["fp64"]["eta_r"], res["mixed"]["eta_r"]
+    rel = abs(e32 / e64 - 1.0)
+    print(f"eta_r fp64 {e64:.6f} mixed {e32:.6f} rel {rel:.2e}")
+    assert e64 > 1.0
+    assert rel <= 1e-2
+    tot64 = res["fp64"]["contact"] + res["fp64"]["lubrication"]
+    tot32 = res["mixed"]["contact"] + res["mixed"]["lubrication"]
+    scale = np.abs(tot64).max()
+    assert np.abs(tot32 - tot64).max() <= 1e-2 * scale

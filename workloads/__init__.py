@@ -218,12 +218,31 @@ def replica_table(R: int = 256, seed: int = 4000, n_lo: int = 500,
                  mu=float(mus[r]), seed=3000 + r) for r in range(R)]
 
 
+def _make_replica(job):
+    r, row, pack_seed, tol, max_sweeps = job
+    return make(row["N"], row["phi"], row["pe"], row["mu"],
+                pack_seed=pack_seed + 2 * r, dyn_seed=row["seed"], tol=tol,
+                name=f"replica{r}", max_sweeps=max_sweeps)
+
+
 def make_replicas(table, pack_seed: int = 5000, tol: float = 1e-4,
-                  max_sweeps: int = 2000):
-    out = []
-    for r, row in enumerate(table):
-        w = make(row["N"], row["phi"], row["pe"], row["mu"],
-                 pack_seed=pack_seed + 2 * r, dyn_seed=row["seed"], tol=tol,
-                 name=f"replica{r}", max_sweeps=max_sweeps)
-        out.append(w)
-    return out
+                  max_sweeps: int = 2000, processes: int = 1):
+    """One workload per row of ``replica_table``; with processes > 1 the
+    packings are made by a pool of freshly spawned interpreters (safe to
+    start after CUDA is initialised), with the same results."""
+    jobs = [(r, row, pack_seed, tol, max_sweeps) for r, row in enumerate(table)]
+    if processes <= 1:
+        return [_make_replica(j) for j in jobs]
+    import multiprocessing as mp
+    build()
+    # one OpenMP thread per worker: the pool supplies the parallelism
+    prev = os.environ.get("OMP_NUM_THREADS")
+    os.environ["OMP_NUM_THREADS"] = "1"
+    try:
+        with mp.get_context("spawn").Pool(processes) as pool:
+            return pool.map(_make_replica, jobs, chunksize=1)
+    finally:
+        if prev is None:
+            os.environ.pop("OMP_NUM_THREADS", None)
+        else:
+            os.environ["OMP_NUM_THREADS"] = prev
