@@ -8,6 +8,9 @@
  * Eqs. 19-24), integrated by Velocity-Verlet (Sec. II, Eqs. 1-2) in a
  * tilted periodic box sheared at a fixed rate with the strain flip of
  * Sec. II.E, and reporting the pair-virial stress (Sec. II.A, II.B, II.D).
+ * Optional: the short-range repulsion of Sec. IV.E (Eq. 34) and the
+ * structural Brownian stress of Sec. II.D (Eqs. 25-26) with its Green-Kubo
+ * viscosity (Sec. III.D, Eq. 33).
  *
  * Conventions used by every call:
  *   - Particles are identified by their tag = index in the caller's arrays.
@@ -87,13 +90,22 @@ typedef struct susp_params {
   int32_t kmax;       /* neighbour row capacity (0: default 48)             */
   int32_t threads_per_particle; /* 0 = autotune, else 1, 2, 4 or 8          */
   int32_t use_graphs; /* 1: replay steps as CUDA graphs (default)           */
-  int32_t reserved[3];
+  int32_t structural; /* 1: sample the structural Brownian stress (Eq. 26)  */
+  int32_t series_cap; /* per replica, samples of Sigma^B_xy kept for        */
+                      /* Green-Kubo (0: none); needs structural = 1         */
+  int32_t reserved;
+  double rep_A;       /* repulsion force scale A of Eq. 34 (0: off);        */
+                      /* batch handles: this replica's A                    */
+  double rep_cut;     /* repulsion acts for h <= rep_cut kappa,             */
+                      /* kappa = 0.01 (a_i + a_j) (default 10)              */
+  double shell;       /* structural shell Delta / a_i (paper: 0.05)         */
 } susp_params;
 
 /* Fills *p with the defaults: eta = rho = 1, kn = 1e4, kt = 0, mu = 0,
  * xi_min = 1e-3, xi_max = 0.05, skin = 0.3, shear_rate = 1, kT = 0,
  * torque_sign = -1, dt = 1e-4, seed = 0, FP64, all terms on, sample_every = 1,
- * kmax = 48, autotuned threads per particle, graphs on. */
+ * kmax = 48, autotuned threads per particle, graphs on, no repulsion
+ * (rep_A = 0, rep_cut = 10), no structural stress (shell = 0.05), no series. */
 void susp_default_params(susp_params* p);
 
 typedef struct susp_s susp_t;
@@ -109,9 +121,9 @@ int susp_create(susp_t** out, int64_t N, const double* radii,
 
 /* R independent replicas stepped together (Sec. II.E: ensembles of 10-800
  * realisations).  N_r[R] sizes, radii[sum N_r], boxes[R][3], p_r[R]
- * parameters (eta, rho, kn, kt, mu, shear_rate, kT, seed may differ per
- * replica; xi_min, xi_max, skin, precision and the switches are taken from
- * p_r[0]). */
+ * parameters (eta, rho, kn, kt, mu, shear_rate, kT, seed, rep_A may differ
+ * per replica; xi_min, xi_max, skin, rep_cut, shell, series_cap, precision
+ * and the switches are taken from p_r[0]). */
 int susp_create_batch(susp_t** out, int32_t R, const int64_t* N_r,
                       const double* radii, const double* boxes,
                       const susp_params* p_r);
@@ -165,11 +177,13 @@ int susp_get_forces(susp_t* h, double* F, double* T);
 
 /* ---- the method ----------------------------------------------------------- */
 /* Cell binning by a counting sort on the cell key, then the skin-padded
- * half neighbour list: every unordered pair with
- * |r|^2 < ((a_i + a_j)(1 + xi_max/2) + skin)^2 (cutoff xi <= xi_max of
- * Sec. II.B plus the skin of Sec. II), stored once; the tangential history
- * of touching pairs is carried over.  Done automatically by the step when
- * the displacement bound exceeds the skin. */
+ * half neighbour list: every unordered pair with |r|^2 < (r_int + skin)^2,
+ * stored once, where r_int is the widest interaction range in use:
+ * (a_i + a_j)(1 + xi_max/2) (lubrication cutoff xi <= xi_max, Sec. II.B),
+ * with repulsion also (a_i + a_j)(1 + 0.01 rep_cut), with the structural
+ * stress also a_i + a_j + shell max(a_i, a_j); the skin is that of Sec. II.
+ * The tangential history of touching pairs is carried over.  Done
+ * automatically by the step when the displacement bound exceeds the skin. */
 int susp_build_neighbors(susp_t* h);
 
 /* Evaluates forces, torques and pair stresses at the current state without
@@ -207,10 +221,14 @@ int susp_profile(susp_t* h, int64_t n_steps, double dt, double* out);
  *   [27..35] drag stresslet (20/3) pi eta sum a^3 E / V (Sec. II.B)
  *   [36..44] kinetic        sum m (U - U_inf)(U - U_inf) / V (full steps)
  *   [45..53] rotational kinetic sum I (W - W_inf)(W - W_inf) / V
- *   [54] eta_r = (sigma^C + sigma^HL + drag)_xy / (eta rate)   (Sec. II.E)
+ *   [54] eta_r = (sigma^C + sigma^HL + drag + sigma^R)_xy / (eta rate)
  *   [55] N1 = sigma_xx - sigma_yy, [56] N2 = sigma_yy - sigma_zz of that sum
- *   [57] number of sampled evaluations */
-#define SUSP_STRESS_LEN 58
+ *   [57] number of sampled evaluations
+ *   [58..66] repulsion      sigma^R (Eq. 34; zero when rep_A = 0)
+ *   [67..75] structural Brownian Sigma^B, Eq. 26: -kT/V sum_i (a_i/Delta)
+ *            sum_{j: h_ij <= Delta} n_ij n_ij with Delta = shell a_i, overlaps
+ *            included (zero unless structural = 1; not added to eta_r) */
+#define SUSP_STRESS_LEN 76
 int susp_stress(susp_t* h, int32_t replica, double* out);
 
 /* The current half neighbour list as tag pairs ij[count][2] with i < j in
@@ -232,6 +250,28 @@ int susp_get_history(susp_t* h, int32_t* ij, double* xi_t, int64_t cap,
  * kernels of each rebuild taken inside a replay). */
 #define SUSP_INFO_LEN 14
 int susp_get_info(susp_t* h, double* info);
+
+/* ---- Green-Kubo (Sec. III.D) -------------------------------------------------- */
+/* The Sigma^B_xy of each sampled evaluation of replica `replica` since the
+ * record was last reset, oldest first: *count receives the number recorded
+ * and *dropped (may be NULL) the number dropped because series_cap samples
+ * were already held.  With out NULL or cap 0 only the counts are returned;
+ * otherwise min(count, cap) samples are copied to out and the record is
+ * reset. */
+int susp_get_series(susp_t* h, int32_t replica, double* out, int64_t cap,
+                    int64_t* count, int64_t* dropped);
+
+/* Green-Kubo viscosity of a stress series x[n] sampled every dt (Eq. 33):
+ * C[m] = sum_{t < n-m} x[t+m] x[t] / (n - m) for m < max_lag (computed on the
+ * current device), eta[m] = V/kT dt sum of the trapezoids of C up to m
+ * (eta[0] = 0), and fit[2] = (eta_phi, tau_phi) of the least-squares fit
+ * eta ~ eta_phi (1 - exp(-t/tau_phi)) over tau_g = dt (10 max_lag)^(g/(G-1)),
+ * g < G = 400.  x is a HOST array; C, eta (max_lag each) and fit are host
+ * outputs (C may be NULL).  Errors: SUSP_EINVAL (NULL, n < 2, max_lag < 2 or
+ * > n, dt, V or kT <= 0), SUSP_ENODEV, SUSP_ENOMEM, SUSP_ECUDA; message in
+ * susp_create_error(). */
+int susp_green_kubo(const double* x, int64_t n, int64_t max_lag, double dt,
+                    double V, double kT, double* C, double* eta, double* fit);
 
 /* ---- without allocation ------------------------------------------------------ */
 /* The paper has no counterpart to this call; it is a service for callers

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libsusp.so")
 SUSP_OK, SUSP_EINVAL, SUSP_ENOMEM, SUSP_ECUDA, SUSP_ESTATE = 0, 1, 2, 3, 4
 SUSP_ENEIGH, SUSP_EUNSTABLE, SUSP_ETIMEOUT, SUSP_ENODEV = 5, 6, 7, 8
 SUSP_FP64, SUSP_MIXED = 0, 1
-SUSP_STRESS_LEN = 58
+SUSP_STRESS_LEN = 76
 SUSP_INFO_LEN = 14
 SUSP_PROFILE_LEN = 15
 PROFILE_FAMILIES = ("integrate", "rebuild", "pair", "reduce", "finalize")
@@ -47,7 +47,9 @@ class susp_params(C.Structure):
         ("lubrication", C.c_int32), ("onebody", C.c_int32),
         ("contact", C.c_int32), ("sample_every", C.c_int32),
         ("kmax", C.c_int32), ("threads_per_particle", C.c_int32),
-        ("use_graphs", C.c_int32), ("reserved", C.c_int32 * 3),
+        ("use_graphs", C.c_int32), ("structural", C.c_int32),
+        ("series_cap", C.c_int32), ("reserved", C.c_int32),
+        ("rep_A", C.c_double), ("rep_cut", C.c_double), ("shell", C.c_double),
     ]
 
 
@@ -86,6 +88,9 @@ _SIGNATURES = {
                                            C.c_void_p, C.c_int64, C.c_void_p, _D,
                                            C.c_double, C.POINTER(susp_params), C.c_double,
                                            C.c_int64, C.c_void_p, C.c_void_p]),
+    "susp_get_series": (C.c_int, [_H, C.c_int32, _D, C.c_int64, _I64, _I64]),
+    "susp_green_kubo": (C.c_int, [_D, C.c_int64, C.c_int64, C.c_double, C.c_double,
+                                  C.c_double, _D, _D, _D]),
     "susp_save": (C.c_int, [_H, C.c_char_p]),
     "susp_load": (C.c_int, [_H, C.c_char_p]),
 }
@@ -131,6 +136,16 @@ def default_params(**kw) -> susp_params:
             raise TypeError(f"unknown parameter {k}")
         setattr(p, k, v)
     return p
+
+
+def green_kubo(x, max_lag: int, dt: float, V: float, kT: float):
+    """Autocorrelation C, running Green-Kubo viscosity eta (Eq. 33) and the
+    fit (eta_phi, tau_phi) of a stress series, computed by the library."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    Cc, eta, fit = np.zeros(max_lag), np.zeros(max_lag), np.zeros(2)
+    check(lib.susp_green_kubo(_dp(x), len(x), int(max_lag), float(dt), float(V), float(kT),
+                              _dp(Cc), _dp(eta), _dp(fit)))
+    return Cc, eta, (float(fit[0]), float(fit[1]))
 
 
 def check(code: int, h=None):
@@ -243,7 +258,20 @@ class System:
         t = out[:54].reshape(6, 3, 3)
         return dict(contact=t[0], lubrication=t[1], brownian=t[2], drag=t[3],
                     kinetic=t[4], kinetic_rot=t[5], eta_r=out[54], N1=out[55],
-                    N2=out[56], samples=int(out[57]))
+                    N2=out[56], samples=int(out[57]),
+                    repulsion=out[58:67].reshape(3, 3), structural=out[67:76].reshape(3, 3))
+
+    def series(self, replica: int = 0):
+        """Sigma^B_xy of each sampled evaluation since the last call (which
+        resets the record), and the number of samples dropped beyond the
+        capacity."""
+        n, dropped = C.c_int64(0), C.c_int64(0)
+        self._chk(lib.susp_get_series(self._h, int(replica), None, 0, C.byref(n),
+                                      C.byref(dropped)))
+        out = np.zeros(max(n.value, 1))
+        self._chk(lib.susp_get_series(self._h, int(replica), _dp(out), n.value, C.byref(n),
+                                      C.byref(dropped)))
+        return out[:n.value], dropped.value
 
     def pairs(self):
         n = C.c_int64(0)

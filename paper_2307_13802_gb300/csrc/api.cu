@@ -115,6 +115,7 @@ void fill_replica_physics(Replica& R, const susp_params& p) {
   R.kn = p.kn;
   R.kt = p.kt;
   R.mu = p.mu;
+  R.rep_A = p.rep_A;
   R.key0 = (uint32_t)(p.seed & 0xffffffffull);
   R.key1 = (uint32_t)(p.seed >> 32);
 }
@@ -137,6 +138,12 @@ int validate_params(const susp_params* p, std::string& msg) {
   }
   if (p->sample_every < 1) { msg = "sample_every must be >= 1"; return SUSP_EINVAL; }
   if (p->kmax < 0 || p->kmax > 64) { msg = "kmax must be in [0, 64]"; return SUSP_EINVAL; }
+  if (!(p->rep_A >= 0) || !std::isfinite(p->rep_A)) { msg = "rep_A must be finite and >= 0"; return SUSP_EINVAL; }
+  if (!(p->rep_cut > 0) || !std::isfinite(p->rep_cut)) { msg = "rep_cut must be > 0"; return SUSP_EINVAL; }
+  if (!(p->shell > 0) || !(p->shell < 1)) { msg = "shell must be in (0, 1)"; return SUSP_EINVAL; }
+  if (p->structural != 0 && p->structural != 1) { msg = "structural must be 0 or 1"; return SUSP_EINVAL; }
+  if (p->series_cap < 0) { msg = "series_cap must be >= 0"; return SUSP_EINVAL; }
+  if (p->series_cap > 0 && !p->structural) { msg = "series_cap needs structural = 1"; return SUSP_EINVAL; }
   const int t = p->threads_per_particle;
   if (!(t == 0 || t == 1 || t == 2 || t == 4 || t == 8)) {
     msg = "threads_per_particle must be 0, 1, 2, 4 or 8"; return SUSP_EINVAL;
@@ -202,8 +209,18 @@ int common_create(susp_t** out, int32_t R, const int64_t* N_r,
       h->rep_of[i] = r;
     }
   }
+  // the widest interaction range, the same expression as the list build's
+  // per-pair cutoff evaluated for the largest pair
   const double xi_max = p_r[0].xi_max;
-  h->rcmax = (h->amax + h->amax) * (1.0 + 0.5 * xi_max);
+  {
+    bool rep_on = false;
+    for (int r = 0; r < R; ++r) rep_on |= p_r[r].rep_A > 0.0;
+    const double S = h->amax + h->amax;
+    double rc = S * (1.0 + 0.5 * xi_max);
+    if (rep_on) rc = std::max(rc, S * (1.0 + 0.01 * p_r[0].rep_cut));
+    if (p_r[0].structural) rc = std::max(rc, S + p_r[0].shell * h->amax);
+    h->rcmax = rc;
+  }
   const double rlist = h->rcmax + p_r[0].skin;
   const double guard = rlist * (1.0 + 1e-9) + 1e-12;
   h->repl_h.resize(R);
@@ -345,7 +362,11 @@ int allocate(susp_t* h) {
   ok &= alloc_n(h, &A.pair_partial, (int64_t)nb * kPartialLen);
   ok &= alloc_n(h, &A.pair_partial_w, (int64_t)nb * kPartialLen);
   ok &= alloc_n(h, &A.kin_partial, (int64_t)nb * kKinLen);
-  ok &= alloc_n(h, &A.stress_acc, (int64_t)h->R * 48);
+  ok &= alloc_n(h, &A.stress_acc, (int64_t)h->R * kAccStride);
+  A.series_cap = h->p0.structural ? h->p0.series_cap : 0;
+  A.shell = h->p0.shell;
+  ok &= alloc_n(h, &A.series, (int64_t)h->R * std::max(A.series_cap, 1));
+  ok &= alloc_n(h, &A.series_n, 2 * (int64_t)h->R);
   ok &= alloc_n(h, &A.rep_bstart, h->R + 1);
   ok &= alloc_n(h, &A.repl, h->R);
   ok &= alloc_n(h, &A.ctl, 1);
@@ -412,6 +433,17 @@ StepArgs make_args(const susp_t* h, double dt, int advance, int sample) {
   s.friction = fric;
   s.advance = advance;
   s.sample = sample;
+  int rep_on = 0;
+  for (const Replica& R : h->repl_h) rep_on |= R.rep_A > 0.0;
+  s.rep_on = rep_on;
+  s.structural = p.structural;
+  s.rep_fac = 1.0 + 0.01 * p.rep_cut;
+  s.rep_cut = p.rep_cut;
+  s.rep_hc = 0.01 * p.rep_cut;
+  s.shell = p.shell;
+  s.rep_fac_f = (float)s.rep_fac;
+  s.rep_hc_f = (float)s.rep_hc;
+  s.shell_f = (float)s.shell;
   s.dt_f = (float)s.dt;
   s.hdt_f = (float)s.hdt;
   s.xi_min_f = (float)s.xi_min;
@@ -782,15 +814,15 @@ int set_state_impl(susp_t* h, const double* x, const double* U, const double* W,
 // checkpoints
 // ---------------------------------------------------------------------------
 // File layout (native byte order, written by this library only):
-//   "SUSPCKP1", int64 N, int32 R, int32 precision, int64 k, int64 steps_done,
+//   "SUSPCKP2", int64 N, int32 R, int32 precision, int64 k, int64 steps_done,
 //   double last_dt, int32 forces_valid, int32 0,
 //   R x susp_params, R x double strain, N x double radius,
 //   5 x [N][3] double: x, U, Omega, F, T (tag order),
-//   R x 48 double stress accumulators,
+//   R x 72 double stress accumulators,
 //   int64 npairs, npairs x (int32 tag_i, int32 tag_j), npairs x 3 double xi_t,
 //   "SUSPEND1".
 // The mixed layout's double-float values convert to and from double exactly.
-constexpr char kCkMagic[8] = {'S', 'U', 'S', 'P', 'C', 'K', 'P', '1'};
+constexpr char kCkMagic[8] = {'S', 'U', 'S', 'P', 'C', 'K', 'P', '2'};
 constexpr char kCkEnd[8] = {'S', 'U', 'S', 'P', 'E', 'N', 'D', '1'};
 
 struct CkHeader {
@@ -807,7 +839,8 @@ bool same_static_params(const susp_params& a, const susp_params& b) {
          a.xi_min == b.xi_min && a.xi_max == b.xi_max && a.skin == b.skin &&
          a.torque_sign == b.torque_sign && a.precision == b.precision && a.noise == b.noise &&
          a.lubrication == b.lubrication && a.onebody == b.onebody && a.contact == b.contact &&
-         a.sample_every == b.sample_every;
+         a.sample_every == b.sample_every && a.rep_A == b.rep_A && a.rep_cut == b.rep_cut &&
+         a.shell == b.shell && a.structural == b.structural;
 }
 
 struct FileCloser {
@@ -833,7 +866,7 @@ int save_checkpoint(susp_t* h, const char* path) {
   }
   Ctl c{};
   std::vector<Replica> rep(h->R);
-  std::vector<double> acc(48 * (size_t)h->R);
+  std::vector<double> acc(kAccStride * (size_t)h->R);
   CK(cudaMemcpyAsync(&c, h->A.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(rep.data(), h->A.repl, sizeof(Replica) * h->R, cudaMemcpyDeviceToHost,
                      h->stream));
@@ -881,7 +914,7 @@ int load_checkpoint(susp_t* h, const char* path) {
   if (hd.precision != h->p0.precision) return bad("precision differs from the handle");
   const int64_t N = h->N;
   std::vector<susp_params> pr(h->R);
-  std::vector<double> strain(h->R), radii(N), st(15 * N), acc(48 * (size_t)h->R);
+  std::vector<double> strain(h->R), radii(N), st(15 * N), acc(kAccStride * (size_t)h->R);
   if (std::fread(pr.data(), sizeof(susp_params), h->R, fc.f) != (size_t)h->R ||
       std::fread(strain.data(), sizeof(double), h->R, fc.f) != (size_t)h->R ||
       std::fread(radii.data(), sizeof(double), N, fc.f) != (size_t)N ||
@@ -1044,6 +1077,11 @@ void susp_default_params(susp_params* p) {
   p->kmax = 48;
   p->threads_per_particle = 0;
   p->use_graphs = 1;
+  p->structural = 0;
+  p->series_cap = 0;
+  p->rep_A = 0.0;
+  p->rep_cut = 10.0;
+  p->shell = 0.05;
 }
 
 int susp_create(susp_t** out, int64_t N, const double* radii, const double box[3],
@@ -1239,15 +1277,16 @@ int susp_stress(susp_t* h, int32_t replica, double* out) {
   if (replica < 0 || replica >= h->R) return fail(h, SUSP_EINVAL, "replica out of range");
   if (!h->allocated) return fail(h, SUSP_ESTATE, "no state yet");
   CK(cudaSetDevice(h->dev));
-  double acc[48];
-  CK(cudaMemcpyAsync(acc, h->A.stress_acc + 48 * (int64_t)replica, sizeof(acc),
+  double acc[kAccStride];
+  CK(cudaMemcpyAsync(acc, h->A.stress_acc + kAccStride * (int64_t)replica, sizeof(acc),
                      cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaMemsetAsync(h->A.stress_acc + 48 * (int64_t)replica, 0, sizeof(acc), h->stream));
+  CK(cudaMemsetAsync(h->A.stress_acc + kAccStride * (int64_t)replica, 0, sizeof(acc),
+                     h->stream));
   CK(cudaStreamSynchronize(h->stream));
   const Replica& R = h->repl_h[replica];
-  const double np = acc[45], nk = acc[46];
+  const double np = acc[kAccNp], nk = acc[kAccNk];
   const double V = R.V;
-  for (int c = 0; c < 27; ++c) out[c] = np > 0 ? acc[c] / np / V : 0.0;
+  for (int c = 0; c < kVirLen; ++c) out[c] = np > 0 ? acc[c] / np / V : 0.0;
   // drag stresslet (20/3) pi eta sum a^3 E / V, E = rate/2 (xy + yx)
   double s3 = 0.0;
   for (int64_t i = h->off[replica]; i < h->off[replica + 1]; ++i)
@@ -1256,13 +1295,109 @@ int susp_stress(susp_t* h, int32_t replica, double* out) {
   for (int c = 0; c < 9; ++c) out[27 + c] = 0.0;
   out[27 + 1] = dxy;
   out[27 + 3] = dxy;
-  for (int c = 0; c < 18; ++c) out[36 + c] = nk > 0 ? acc[27 + c] / nk / V : 0.0;
+  for (int c = 0; c < kKinLen; ++c) out[36 + c] = nk > 0 ? acc[kPartialLen + c] / nk / V : 0.0;
+  // repulsion virial; structural sums sum w n n scaled by -kT / (shell V)
+  // (Eq. 26 with a_i / Delta = 1 / shell)
+  for (int c = 0; c < 9; ++c) {
+    out[58 + c] = np > 0 ? acc[kRepOff + c] / np / V : 0.0;
+    out[67 + c] = np > 0 ? -R.kT / h->p0.shell * acc[kStrOff + c] / np / V : 0.0;
+  }
   double tot[9];
-  for (int c = 0; c < 9; ++c) tot[c] = out[c] + out[9 + c] + out[27 + c];
+  for (int c = 0; c < 9; ++c) tot[c] = out[c] + out[9 + c] + out[27 + c] + out[58 + c];
   out[54] = R.rate != 0.0 ? tot[1] / (R.eta * R.rate) : 0.0;
   out[55] = tot[0] - tot[4];
   out[56] = tot[4] - tot[8];
   out[57] = np;
+  return SUSP_OK;
+}
+
+int susp_get_series(susp_t* h, int32_t replica, double* out, int64_t cap, int64_t* count,
+                    int64_t* dropped) {
+  if (!h || !count) return SUSP_EINVAL;
+  h->err.clear();
+  if (replica < 0 || replica >= h->R) return fail(h, SUSP_EINVAL, "replica out of range");
+  if (!h->allocated) return fail(h, SUSP_ESTATE, "no state yet");
+  if (h->A.series_cap == 0) return fail(h, SUSP_ESTATE, "no series: create with structural = 1 and series_cap > 0");
+  CK(cudaSetDevice(h->dev));
+  long long nd[2];
+  CK(cudaMemcpyAsync(nd, h->A.series_n + 2 * (int64_t)replica, sizeof(nd),
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const int64_t n = std::min<int64_t>(nd[0], h->A.series_cap);
+  *count = n;
+  if (dropped) *dropped = nd[1];
+  if (!out || cap <= 0) return SUSP_OK;  // count only
+  if (n > 0)
+    CK(cudaMemcpyAsync(out, h->A.series + (int64_t)replica * h->A.series_cap,
+                       sizeof(double) * std::min<int64_t>(n, cap), cudaMemcpyDeviceToHost,
+                       h->stream));
+  CK(cudaMemsetAsync(h->A.series_n + 2 * (int64_t)replica, 0, sizeof(nd), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SUSP_OK;
+}
+
+int susp_green_kubo(const double* x, int64_t n, int64_t max_lag, double dt, double V,
+                    double kT, double* C, double* eta, double* fit) {
+  g_create_error.clear();
+  if (!x || !eta || !fit || n < 2 || max_lag < 2 || max_lag > n || !(dt > 0) || !(V > 0) ||
+      !(kT > 0)) {
+    g_create_error = "green_kubo: need x, eta, fit, n >= 2, 2 <= max_lag <= n and dt, V, kT > 0";
+    return SUSP_EINVAL;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    g_create_error = "no CUDA device";
+    return SUSP_ENODEV;
+  }
+  double *dx = nullptr, *dC = nullptr;
+  if (cudaMalloc(&dx, sizeof(double) * n) != cudaSuccess ||
+      cudaMalloc(&dC, sizeof(double) * max_lag) != cudaSuccess) {
+    cudaFree(dx);
+    g_create_error = "green_kubo: device allocation failed";
+    return SUSP_ENOMEM;
+  }
+  std::vector<double> Ch(max_lag);
+  cudaError_t e = cudaMemcpy(dx, x, sizeof(double) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    launch_autocorr(dx, n, max_lag, dC, nullptr);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpy(Ch.data(), dC, sizeof(double) * max_lag, cudaMemcpyDeviceToHost);
+  cudaFree(dx);
+  cudaFree(dC);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("green_kubo: ") + cudaGetErrorString(e);
+    return SUSP_ECUDA;
+  }
+  // running trapezoid integral, Eq. 33
+  const double pref = V / kT;
+  eta[0] = 0.0;
+  for (int64_t m = 1; m < max_lag; ++m) eta[m] = eta[m - 1] + pref * dt * 0.5 * (Ch[m - 1] + Ch[m]);
+  if (C) std::memcpy(C, Ch.data(), sizeof(double) * max_lag);
+  // eta ~ eta_phi (1 - exp(-t / tau_phi)): least squares on a log grid of tau
+  const int G = 400;
+  double best = -1.0;
+  for (int g = 0; g < G; ++g) {
+    const double tau = dt * std::pow(10.0 * (double)max_lag, (double)g / (double)(G - 1));
+    double sff = 0.0, sef = 0.0;
+    for (int64_t m = 0; m < max_lag; ++m) {
+      const double f = 1.0 - std::exp(-(double)m * dt / tau);
+      sff += f * f;
+      sef += eta[m] * f;
+    }
+    const double ephi = sff > 0.0 ? sef / sff : 0.0;
+    double res = 0.0;
+    for (int64_t m = 0; m < max_lag; ++m) {
+      const double d = eta[m] - ephi * (1.0 - std::exp(-(double)m * dt / tau));
+      res += d * d;
+    }
+    if (best < 0.0 || res < best) {
+      best = res;
+      fit[0] = ephi;
+      fit[1] = tau;
+    }
+  }
   return SUSP_OK;
 }
 

@@ -1,8 +1,10 @@
 // k_neighbors.cu -- cell binning, counting sort and the skin-padded half
 // neighbour list (Sec. II: pairwise forces are summed over the neighbours of
-// each sphere, found within the lubrication cutoff xi <= xi_max of Sec. II.B
-// plus a skin), with the tangential contact history (Sec. II.A) carried from
-// the old list to the new one.
+// each sphere, found within the widest interaction range in use -- the
+// lubrication cutoff xi <= xi_max of Sec. II.B, the repulsion range of
+// Eq. 34, the structural shell of Eq. 26 -- plus a skin), with the
+// tangential contact history (Sec. II.A) carried from the old list to the
+// new one.
 //
 // Cells are laid on the tilted lattice in fractional coordinates
 // s = H^-1 x (H the box matrix with the current tilt), nc cells per axis
@@ -246,7 +248,18 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Arrays A, StepArgs s, dou
           double rr[3], sy;
           min_image_f64(Q.x - P.x, Q.y - P.y, Q.z - P.z, L, tilt, rr, &sy);
           const double d2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
-          const double rc = (P.w + Q.w) * rc_fac + s.skin;
+          // widest interaction range of the pair (lubrication cutoff,
+          // repulsion range, structural shell), then the skin
+          double rc = (P.w + Q.w) * rc_fac;
+          if (s.rep_on) {
+            const double rr = (P.w + Q.w) * s.rep_fac;
+            if (rr > rc) rc = rr;
+          }
+          if (s.structural) {
+            const double rs = (P.w + Q.w) + s.shell * (P.w > Q.w ? P.w : Q.w);
+            if (rs > rc) rc = rs;
+          }
+          rc = rc + s.skin;
           if (!(d2 < rc * rc)) continue;
           if (cnt < kmax) row[(int64_t)cnt * Np] = q;
           ++cnt;

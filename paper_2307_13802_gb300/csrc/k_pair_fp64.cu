@@ -16,6 +16,11 @@
 // noise, Eqs. 20-21) stay in registers; the partner's share is added with
 // double atomics.  On sampled evaluations the pair virials F (x) r of the
 // three components are reduced per block (Sec. II.A, II.B, II.D).
+// Optional terms: the short-range repulsion of Eq. 34 (read as the force on
+// j, so -(A/kappa) exp(-h/kappa) n on i) for h <= rep_cut kappa, with its
+// own virial; and on sampled evaluations the structural Brownian sums of
+// Eq. 26, sum over pairs of w n n with w the number of the two spheres whose
+// shell h <= shell a holds the pair (scaled by -kT / (shell V) on the host).
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
@@ -92,7 +97,12 @@ k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
       const double S = ap + Q.w;
       const double h = d - S;
       const double xi = 2.0 * h / S;
-      if (xi > s.xi_max) continue;
+      const double kappa = 0.01 * S;
+      const bool lub = xi <= s.xi_max;
+      const bool rep = s.rep_on && RP.rep_A > 0.0 && h <= s.rep_cut * kappa;
+      const bool shp = SAMPLE && s.structural && h <= s.shell * ap;
+      const bool shq = SAMPLE && s.structural && h <= s.shell * Q.w;
+      if (!lub && !rep && !shp && !shq) continue;
 
       const double4_32a VQ = A.vel[cur][q];
       const double4_32a WQ = A.omg[cur][q];
@@ -116,8 +126,22 @@ k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
       const double dU[3] = {Uj[0] - syij * rate * L[1] - Ui[0], Uj[1] - Ui[1],
                             Uj[2] - Ui[2]};
 
+      if (SAMPLE && (shp || shq)) {
+        const double w = (shp ? 1.0 : 0.0) + (shq ? 1.0 : 0.0);
+#pragma unroll
+        for (int al = 0; al < 3; ++al)
+#pragma unroll
+          for (int be = 0; be < 3; ++be) vir[kStrOff + 3 * al + be] += w * n[al] * n[be];
+      }
+      double FR[3] = {0.0, 0.0, 0.0};
+      if (rep) {
+        const double f = RP.rep_A / kappa * exp(-h / kappa);
+#pragma unroll
+        for (int q3 = 0; q3 < 3; ++q3) FR[q3] = -f * n[q3];
+      }
+
       PairOut<double> o;
-      if (s.lubrication) {
+      if (lub && s.lubrication) {
         const double xi_e = xi < s.xi_min ? s.xi_min : xi;
         const double lg = log(1.0 / xi_e);
         const Res8<double> R = resistances<double>(eta, ai, aj, xi_e, lg);
@@ -167,7 +191,7 @@ k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
       double Fi[3], Ti_[3], Tj_[3];
 #pragma unroll
       for (int q3 = 0; q3 < 3; ++q3) {
-        Fi[q3] = FC[q3] + o.FL[q3] + o.FB[q3];
+        Fi[q3] = FC[q3] + o.FL[q3] + o.FB[q3] + FR[q3];
         Ti_[q3] = TCi[q3] + o.Ti[q3];
         Tj_[q3] = TCj[q3] + o.Tj[q3];
       }
@@ -197,6 +221,7 @@ k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
             vir[3 * al + be] += FC[al] * rr[be];
             vir[9 + 3 * al + be] += o.FL[al] * rr[be];
             vir[18 + 3 * al + be] += o.FB[al] * rr[be];
+            vir[kRepOff + 3 * al + be] += FR[al] * rr[be];
           }
       }
     }

@@ -23,8 +23,6 @@
 //     precision, block, global and time sums in double.
 #include <cuda_runtime.h>
 
-#include <type_traits>
-
 #include "device_common.cuh"
 #include "dfloat.cuh"
 #include "philox.cuh"
@@ -136,7 +134,9 @@ __device__ __forceinline__ int wrap_dc(int d, int n) {
 #define SUSP_PAIR_MINBLOCKS 3
 #endif
 
-template <bool NOISE, bool FRIC, bool SAMPLE>
+// EXTRA: the optional repulsion (Eq. 34) and structural sums (Eq. 26) are
+// compiled in; without them the kernel keeps the smaller body
+template <bool NOISE, bool FRIC, bool SAMPLE, bool EXTRA>
 __global__ void __launch_bounds__(kBlock, SUSP_PAIR_MINBLOCKS)
 k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   constexpr unsigned kFull = 0xffffffffu;
@@ -150,6 +150,9 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   const int r = bm.rep[b];
   const Replica& RP = A.repl[r];
   if (threadIdx.x == 0) sArrive = 0;
+  // per-warp block-partial slots; the repulsion and structural parts are
+  // accumulated into them while the warp works
+  for (int i = threadIdx.x; i < (kBlock / 32) * kPartialLen; i += kBlock) sW[i] = 0.0f;
   if (threadIdx.x < 9) {
     const float fx = (float)((int)threadIdx.x / 3 - 1), fy = (float)((int)threadIdx.x % 3 - 1);
     const df v = df_add(df{RP.cw_hi[0] * fx, RP.cw_lo[0] * fx}, df{RP.ct_hi * fy, RP.ct_lo * fy});
@@ -173,7 +176,14 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   const int64_t Np = A.Npad;
   const int64_t hs = (int64_t)A.kmax * Np;
   const float xi_min = s.xi_min_f, xi_max = s.xi_max_f;
-  const float rc_fac = 1.0f + 0.5f * xi_max;
+  // optional terms: repulsion (Eq. 34) of this replica, structural sums
+  // (Eq. 26) on sampled steps; rcf and shf widen the single-precision range
+  // test to the widest interaction range in use
+  const bool rep_on = EXTRA && s.rep_on && RP.rep_A_f > 0.0f;
+  const float repA = RP.rep_A_f, rep_hc = s.rep_hc_f;
+  const bool strc = EXTRA && SAMPLE && s.structural;
+  const float shf = strc ? s.shell_f : 0.0f;
+  const float rcf = rep_on ? fmaxf(1.0f + 0.5f * xi_max, s.rep_fac_f) : 1.0f + 0.5f * xi_max;
   const float tsign = s.tsign_f;
   const float dtf = s.dt_f;
   const float pi = 3.14159265358979f;
@@ -225,9 +235,9 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   const int excl = incl - nn;
   __syncwarp();
 
-  float vir[SAMPLE ? kPartialLen : 1];
+  float vir[SAMPLE ? kVirLen : 1];
 #pragma unroll
-  for (int q = 0; q < (SAMPLE ? kPartialLen : 1); ++q) vir[q] = 0.0f;
+  for (int q = 0; q < (SAMPLE ? kVirLen : 1); ++q) vir[q] = 0.0f;
 
   // Pairs within the cutoff are queued per warp in shared memory, touching
   // pairs (queue 1) apart from the others (queue 0), and the pair physics
@@ -239,11 +249,11 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   __shared__ float qG[2][kBlock / 32][6][kQ];   // r_x, r_y, r_z, d, h, S
   int qn0 = 0, qn1 = 0;
 
-  // Pair e of queue CT: partner's share by vector reductions, owner's share
-  // returned in v (force, torque) with its contact bit; returns the owner.
-  auto physics = [&](auto CT, int e, float* v, unsigned long long& mbit) -> int {
-    constexpr bool CONTACT = decltype(CT)::value;
-    constexpr int qi = CONTACT ? 1 : 0;
+  // Pair e of queue qi (1: touching pairs): partner's share by vector
+  // reductions, owner's share returned in v (force, torque) with its contact
+  // bit; returns the owner.  qi is warp-uniform.
+  auto physics = [&](int qi, int e, float* v, unsigned long long& mbit, float* FR,
+                     float* rro) -> int {
     const int q = qQ[qi][warp][e];
     const int meta = qM[qi][warp][e];
     const int o = meta & 31, sl = (meta >> 5) & 127;
@@ -268,7 +278,18 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
     const float dU[3] = {Vj.x - Vi.x + rate * rr[1], Vj.y - Vi.y, Vj.z - Vi.z};
 
     PairOut<float> ou;
-    if (s.lubrication) {
+    // repulsion, Eq. 34 read as the force on j: -(A/kappa) exp(-h/kappa) n on i
+    FR[0] = FR[1] = FR[2] = 0.0f;
+    if (rep_on) {
+      const float kap = 0.01f * S;
+      if (h <= rep_hc * S) {
+        const float f = repA / kap * __expf(-h / kap);
+        FR[0] = -f * n[0]; FR[1] = -f * n[1]; FR[2] = -f * n[2];
+      }
+    }
+    rro[0] = rr[0]; rro[1] = rr[1]; rro[2] = rr[2];
+    // queued pairs beyond the lubrication cutoff exist only with repulsion
+    if (s.lubrication && (!EXTRA || xi <= xi_max)) {
       const float xi_e = fmaxf(xi, xi_min);
       const float ixi = 1.0f / xi_e;
       const float L = __logf(ixi);
@@ -286,7 +307,7 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
     }
     float FC[3] = {0.f, 0.f, 0.f}, TCi[3] = {0.f, 0.f, 0.f}, TCj[3] = {0.f, 0.f, 0.f};
     mbit = 0ull;
-    if constexpr (CONTACT) {
+    if (qi == 1) {
       const float delta = -h;
       float Ft[3] = {0.f, 0.f, 0.f};
       if (FRIC && mu > 0.0f) {
@@ -325,7 +346,7 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
     float Fi[3], Ti_[3], Tj_[3];
 #pragma unroll
     for (int q3 = 0; q3 < 3; ++q3) {
-      Fi[q3] = FC[q3] + ou.FL[q3] + ou.FB[q3];
+      Fi[q3] = FC[q3] + ou.FL[q3] + ou.FB[q3] + FR[q3];
       Ti_[q3] = TCi[q3] + ou.Ti[q3];
       Tj_[q3] = TCj[q3] + ou.Tj[q3];
     }
@@ -340,7 +361,7 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
       for (int al = 0; al < 3; ++al)
 #pragma unroll
         for (int be = 0; be < 3; ++be) {
-          if constexpr (CONTACT) vir[3 * al + be] += FC[al] * rr[be];
+          vir[3 * al + be] += FC[al] * rr[be];
           vir[9 + 3 * al + be] += ou.FL[al] * rr[be];
           vir[18 + 3 * al + be] += ou.FB[al] * rr[be];
         }
@@ -349,16 +370,28 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   };
 
   // One batch of `count` (warp-uniform, 1..32) consecutive entries of queue
-  // CT.  Queue entries are in row order, so the owners along a batch are
+  // qi.  Queue entries are in row order, so the owners along a batch are
   // non-decreasing: the owner's shares are summed over each run of equal
   // owners by shuffles, and the run's first lane adds the sums to the
   // owner's shared-memory accumulators (one writer per owner per batch).
-  auto batch = [&](auto CT, int first, int count) {
-    constexpr bool CONTACT = decltype(CT)::value;
+  auto batch = [&](int qi, int first, int count) {
     float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     unsigned long long mb = 0ull;
     int own = 32;  // idle lanes: past every owner
-    if (lane < count) own = physics(CT, first + lane, v, mb);
+    float FR[3] = {0.f, 0.f, 0.f}, rro[3] = {0.f, 0.f, 0.f};
+    if (lane < count) own = physics(qi, first + lane, v, mb, FR, rro);
+    if (SAMPLE && rep_on) {
+      // repulsion virial F^R (x) r summed over the warp into its slots
+#pragma unroll
+      for (int al = 0; al < 3; ++al)
+#pragma unroll
+        for (int be = 0; be < 3; ++be) {
+          float x = FR[al] * rro[be];
+#pragma unroll
+          for (int o2 = 16; o2 > 0; o2 >>= 1) x += __shfl_down_sync(kFull, x, o2);
+          if (lane == 0) sW[warp * kPartialLen + kRepOff + 3 * al + be] += x;
+        }
+    }
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
       const int oo = __shfl_down_sync(kFull, own, off);
@@ -369,7 +402,7 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
         const float x = __shfl_down_sync(kFull, v[cc], off);
         if (same) v[cc] += x;
       }
-      if (FRIC && CONTACT) {
+      if (FRIC && qi == 1) {
         const unsigned long long x = __shfl_down_sync(kFull, mb, off);
         if (same) mb |= x;
       }
@@ -383,109 +416,142 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
       t.x += v[3]; t.y += v[4]; t.z += v[5];
       *so = f;
       *st = t;
-      if (FRIC && CONTACT) sM[warp * 32 + own] |= mb;
+      if (FRIC && qi == 1) sM[warp * 32 + own] |= mb;
     }
     __syncwarp();
   };
 
-  for (int base = 0; base < total; base += 32) {
-    const int t = base + lane;
-    // owner lane: first lane whose inclusive row end exceeds t
-    int o = 0;
+  // Work loop of the warp, all decisions warp-uniform: flush a queue that
+  // holds a full batch, else scan the next 32 list items into the queues,
+  // else drain what is left.  Phase A and the pair physics each have a
+  // single call site, so the kernel body stays small in instruction cache.
+  int base = 0;
+  while (true) {
+    int qi = -1, first = 0, count = 0;
+    if (qn0 >= 32) {
+      qi = 0; first = qn0 - 32; count = 32;
+    } else if (qn1 >= 32) {
+      qi = 1; first = qn1 - 32; count = 32;
+    } else if (base < total) {
+      const int t = base + lane;
+      // owner lane: first lane whose inclusive row end exceeds t
+      int o = 0;
 #pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-      const int v = __shfl_sync(kFull, incl, o + step - 1);
-      if (v <= t) o += step;
-    }
-    const int oexcl = __shfl_sync(kFull, excl, o);
-    const unsigned long long ocm = FRIC ? __shfl_sync(kFull, cm_own, o) : 0ull;
-    bool keep = false, touch = false;
-    int q = 0, sl = 0;
-    float gq[6];
-    if (t < total) {
-      sl = t - oexcl;
-      const int po = pb + warp * 32 + o;
-      q = __ldg(nbr + (int64_t)sl * Np + po);
-      const float4 P = __ldg(PM + 2 * po), Q = __ldg(PM + 2 * q);
-      int pcx, pcy, pcz, qcx, qcy, qcz;
-      unpack_cell(__float_as_int(__ldg(&OM[po].w)), pcx, pcy, pcz);
-      unpack_cell(__float_as_int(__ldg(&OM[q].w)), qcx, qcy, qcz);
-      const int dcx = wrap_dc(qcx - pcx, ncx), dcy = wrap_dc(qcy - pcy, ncy),
-                dcz = wrap_dc(qcz - pcz, ncz);
-      const float r0 = (Q.x - P.x) + (cwx * (float)dcx + ctilt * (float)dcy);
-      const float r1 = (Q.y - P.y) + cwy * (float)dcy;
-      const float r2 = (Q.z - P.z) + cwz * (float)dcz;
-      const float d2f = r0 * r0 + r1 * r1 + r2 * r2;
-      const float rc = (P.w + Q.w) * rc_fac;
-      // beyond the lubrication cutoff (with a margin for single-precision
-      // rounding; the exact test follows): no force, no contact
-      if (d2f <= rc * rc * 1.00001f) {
-        // separation in double-float from the cell-relative offsets, then
-        // d^2 - S^2 with the cancelling squares summed error-free, and the
-        // gap h = (d^2 - S^2) / (d + S)
-        const float4 Pl = __ldg(PM + 2 * po + 1), Ql = __ldg(PM + 2 * q + 1);
-        const float2 shx = sShx[(dcx + 1) * 3 + (dcy + 1)];
-        const float fy = (float)dcy, fz = (float)dcz;
-        float rh[3], rl[3];
-        df_diff_shift(Q.x, Ql.x, P.x, Pl.x, shx.x, shx.y, rh[0], rl[0]);
-        df_diff_shift(Q.y, Ql.y, P.y, Pl.y, cw1h * fy, cw1l * fy, rh[1], rl[1]);
-        df_diff_shift(Q.z, Ql.z, P.z, Pl.z, cw2h * fz, cw2l * fz, rh[2], rl[2]);
-        float Sh, Sl;
-        {
-          float s0, e0;
-          two_sum(P.w, Q.w, s0, e0);
-          fast_two_sum(s0, __fadd_rn(e0, __fadd_rn(Pl.w, Ql.w)), Sh, Sl);
-        }
-        float pk[3], ek[3];
+      for (int step = 16; step > 0; step >>= 1) {
+        const int v = __shfl_sync(kFull, incl, o + step - 1);
+        if (v <= t) o += step;
+      }
+      const int oexcl = __shfl_sync(kFull, excl, o);
+      const unsigned long long ocm = FRIC ? __shfl_sync(kFull, cm_own, o) : 0ull;
+      bool keep = false, touch = false;
+      float wst = 0.0f, dst = 1.0f, rst[3] = {0.f, 0.f, 0.f};
+      int q = 0, sl = 0;
+      float gq[6];
+      if (t < total) {
+        sl = t - oexcl;
+        const int po = pb + warp * 32 + o;
+        q = __ldg(nbr + (int64_t)sl * Np + po);
+        const float4 P = __ldg(PM + 2 * po), Q = __ldg(PM + 2 * q);
+        int pcx, pcy, pcz, qcx, qcy, qcz;
+        unpack_cell(__float_as_int(__ldg(&OM[po].w)), pcx, pcy, pcz);
+        unpack_cell(__float_as_int(__ldg(&OM[q].w)), qcx, qcy, qcz);
+        const int dcx = wrap_dc(qcx - pcx, ncx), dcy = wrap_dc(qcy - pcy, ncy),
+                  dcz = wrap_dc(qcz - pcz, ncz);
+        const float r0 = (Q.x - P.x) + (cwx * (float)dcx + ctilt * (float)dcy);
+        const float r1 = (Q.y - P.y) + cwy * (float)dcy;
+        const float r2 = (Q.z - P.z) + cwz * (float)dcz;
+        const float d2f = r0 * r0 + r1 * r1 + r2 * r2;
+        const float rc = EXTRA ? fmaf(shf, fmaxf(P.w, Q.w), (P.w + Q.w) * rcf)
+                               : (P.w + Q.w) * rcf;
+        // beyond the lubrication cutoff (with a margin for single-precision
+        // rounding; the exact test follows): no force, no contact
+        if (d2f <= rc * rc * 1.00001f) {
+          // separation in double-float from the cell-relative offsets, then
+          // d^2 - S^2 with the cancelling squares summed error-free, and the
+          // gap h = (d^2 - S^2) / (d + S)
+          const float4 Pl = __ldg(PM + 2 * po + 1), Ql = __ldg(PM + 2 * q + 1);
+          const float2 shx = sShx[(dcx + 1) * 3 + (dcy + 1)];
+          const float fy = (float)dcy, fz = (float)dcz;
+          float rh[3], rl[3];
+          df_diff_shift(Q.x, Ql.x, P.x, Pl.x, shx.x, shx.y, rh[0], rl[0]);
+          df_diff_shift(Q.y, Ql.y, P.y, Pl.y, cw1h * fy, cw1l * fy, rh[1], rl[1]);
+          df_diff_shift(Q.z, Ql.z, P.z, Pl.z, cw2h * fz, cw2l * fz, rh[2], rl[2]);
+          float Sh, Sl;
+          {
+            float s0, e0;
+            two_sum(P.w, Q.w, s0, e0);
+            fast_two_sum(s0, __fadd_rn(e0, __fadd_rn(Pl.w, Ql.w)), Sh, Sl);
+          }
+          float pk[3], ek[3];
 #pragma unroll
-        for (int k3 = 0; k3 < 3; ++k3) {
-          pk[k3] = __fmul_rn(rh[k3], rh[k3]);
-          ek[k3] = __fmaf_rn(rh[k3], rh[k3], -pk[k3]);
-        }
-        const float pS = __fmul_rn(Sh, Sh);
-        const float eS = __fmaf_rn(Sh, Sh, -pS);
-        float t1, u1, t2, u2, t3, u3;
-        two_sum(pk[0], pk[1], t1, u1);
-        two_sum(t1, pk[2], t2, u2);
-        two_sum(t2, -pS, t3, u3);
-        const float small = ((u1 + u2) + u3) + ((ek[0] + ek[1]) + (ek[2] - eS)) +
-                            2.0f * ((rh[0] * rl[0] + rh[1] * rl[1]) + (rh[2] * rl[2] - Sh * Sl));
-        const float D = __fadd_rn(t3, small);
-        const float d = sqrtf(t2);
-        const float h = D / (d + Sh);
-        if (2.0f * h / Sh <= xi_max) {
-          keep = true;
-          touch = s.contact && h < 0.0f;
-          gq[0] = rh[0]; gq[1] = rh[1]; gq[2] = rh[2];
-          gq[3] = d; gq[4] = h; gq[5] = Sh;
+          for (int k3 = 0; k3 < 3; ++k3) {
+            pk[k3] = __fmul_rn(rh[k3], rh[k3]);
+            ek[k3] = __fmaf_rn(rh[k3], rh[k3], -pk[k3]);
+          }
+          const float pS = __fmul_rn(Sh, Sh);
+          const float eS = __fmaf_rn(Sh, Sh, -pS);
+          float t1, u1, t2, u2, t3, u3;
+          two_sum(pk[0], pk[1], t1, u1);
+          two_sum(t1, pk[2], t2, u2);
+          two_sum(t2, -pS, t3, u3);
+          const float small = ((u1 + u2) + u3) + ((ek[0] + ek[1]) + (ek[2] - eS)) +
+                              2.0f * ((rh[0] * rl[0] + rh[1] * rl[1]) + (rh[2] * rl[2] - Sh * Sl));
+          const float D = __fadd_rn(t3, small);
+          const float d = sqrtf(t2);
+          const float h = D / (d + Sh);
+          if (strc) {
+            // shells h <= shell a of the two spheres (Eq. 26)
+            wst = (h <= shf * P.w ? 1.0f : 0.0f) + (h <= shf * Q.w ? 1.0f : 0.0f);
+            rst[0] = rh[0]; rst[1] = rh[1]; rst[2] = rh[2];
+            dst = d;
+          }
+          if (2.0f * h / Sh <= xi_max || (rep_on && h <= rep_hc * Sh)) {
+            keep = true;
+            touch = s.contact && h < 0.0f;
+            gq[0] = rh[0]; gq[1] = rh[1]; gq[2] = rh[2];
+            gq[3] = d; gq[4] = h; gq[5] = Sh;
+          }
         }
       }
-    }
-    const unsigned m0 = __ballot_sync(kFull, keep && !touch);
-    const unsigned m1 = __ballot_sync(kFull, touch);
-    if (keep) {
-      const unsigned below = (1u << lane) - 1u;
-      const int qi = touch ? 1 : 0;
-      const int e = touch ? qn1 + __popc(m1 & below) : qn0 + __popc(m0 & below);
-      qQ[qi][warp][e] = q;
-      qM[qi][warp][e] = o | (sl << 5) | ((FRIC && ((ocm >> sl) & 1ull)) ? (1 << 12) : 0);
+      if (strc) {
+        // structural sums w n n of these 32 items (6 distinct entries)
+        const float id2 = wst / (dst * dst);
+        const float e6[6] = {rst[0] * rst[0] * id2, rst[0] * rst[1] * id2, rst[0] * rst[2] * id2,
+                             rst[1] * rst[1] * id2, rst[1] * rst[2] * id2, rst[2] * rst[2] * id2};
 #pragma unroll
-      for (int c6 = 0; c6 < 6; ++c6) qG[qi][warp][c6][e] = gq[c6];
+        for (int c6 = 0; c6 < 6; ++c6) {
+          float x = e6[c6];
+#pragma unroll
+          for (int o2 = 16; o2 > 0; o2 >>= 1) x += __shfl_down_sync(kFull, x, o2);
+          if (lane == 0) sW[warp * kPartialLen + kStrOff + c6] += x;
+        }
+      }
+      const unsigned m0 = __ballot_sync(kFull, keep && !touch);
+      const unsigned m1 = __ballot_sync(kFull, touch);
+      if (keep) {
+        const unsigned below = (1u << lane) - 1u;
+        const int qk = touch ? 1 : 0;
+        const int e = touch ? qn1 + __popc(m1 & below) : qn0 + __popc(m0 & below);
+        qQ[qk][warp][e] = q;
+        qM[qk][warp][e] = o | (sl << 5) | ((FRIC && ((ocm >> sl) & 1ull)) ? (1 << 12) : 0);
+#pragma unroll
+        for (int c6 = 0; c6 < 6; ++c6) qG[qk][warp][c6][e] = gq[c6];
+      }
+      qn0 += __popc(m0);
+      qn1 += __popc(m1);
+      __syncwarp();
+      base += 32;
+      continue;
+    } else if (qn0 > 0) {
+      qi = 0; count = qn0;
+    } else if (qn1 > 0) {
+      qi = 1; count = qn1;
+    } else {
+      break;
     }
-    qn0 += __popc(m0);
-    qn1 += __popc(m1);
-    __syncwarp();
-    if (qn0 >= 32) {
-      batch(std::false_type{}, qn0 - 32, 32);
-      qn0 -= 32;
-    }
-    if (qn1 >= 32) {
-      batch(std::true_type{}, qn1 - 32, 32);
-      qn1 -= 32;
-    }
+    batch(qi, first, count);
+    if (qi == 0) qn0 -= count; else qn1 -= count;
   }
-  if (qn0 > 0) batch(std::false_type{}, 0, qn0);
-  if (qn1 > 0) batch(std::true_type{}, 0, qn1);
   // the warp's own accumulators are complete once its batches are done
   if (active) {
     const float4 f = sF[tid], t = sT[tid];
@@ -499,7 +565,7 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
     // block partial, so no warp waits at a block-wide barrier.  Blocks,
     // replicas and time are summed in double by the reduction kernel.
 #pragma unroll
-    for (int cc = 0; cc < kPartialLen; ++cc) {
+    for (int cc = 0; cc < kVirLen; ++cc) {
       float x = vir[cc];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
@@ -511,33 +577,44 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
     arrived = __shfl_sync(kFull, arrived, 0);
     if (arrived == kBlock / 32 - 1) {
       __threadfence_block();
-      if (lane < kPartialLen) {
+      // the structural slots hold the 6 distinct entries of the symmetric
+      // tensor: entry (a, b) of the 3x3 block is slot kSym[3a + b]
+      constexpr int kSym[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
+      for (int cc = lane; cc < kPartialLen; cc += 32) {
+        const int src = cc < kStrOff ? cc : kStrOff + kSym[cc - kStrOff];
         float sum = 0.0f;
         for (int w = 0; w < kBlock / 32; ++w)
-          sum += *(volatile float*)&sW[w * kPartialLen + lane];
-        A.pair_partial_w[(int64_t)b * kPartialLen + lane] = sum;
+          sum += *(volatile float*)&sW[w * kPartialLen + src];
+        A.pair_partial_w[(int64_t)b * kPartialLen + cc] = sum;
       }
     }
   }
 }
 
-template <bool NOISE, bool FRIC>
+template <bool NOISE, bool FRIC, bool EXTRA>
 static void launch_pm(const Arrays& A, const BlockMap& bm, const StepArgs& s,
                       cudaStream_t st) {
   if (s.sample)
-    k_pair_mixed<NOISE, FRIC, true><<<bm.nblocks, kBlock, 0, st>>>(A, bm, s);
+    k_pair_mixed<NOISE, FRIC, true, EXTRA><<<bm.nblocks, kBlock, 0, st>>>(A, bm, s);
   else
-    k_pair_mixed<NOISE, FRIC, false><<<bm.nblocks, kBlock, 0, st>>>(A, bm, s);
+    k_pair_mixed<NOISE, FRIC, false, EXTRA><<<bm.nblocks, kBlock, 0, st>>>(A, bm, s);
+}
+
+template <bool EXTRA>
+static void launch_pm_extra(const Arrays& A, const BlockMap& bm, const StepArgs& s,
+                            cudaStream_t st) {
+  const bool noise = s.noise != 0, fric = s.friction != 0;
+  if (noise && fric) launch_pm<true, true, EXTRA>(A, bm, s, st);
+  else if (noise) launch_pm<true, false, EXTRA>(A, bm, s, st);
+  else if (fric) launch_pm<false, true, EXTRA>(A, bm, s, st);
+  else launch_pm<false, false, EXTRA>(A, bm, s, st);
 }
 
 void launch_pair_mixed(const Arrays& A, const BlockMap& bm, const StepArgs& s, int tpp,
                        cudaStream_t st) {
   (void)tpp;
-  const bool noise = s.noise != 0, fric = s.friction != 0;
-  if (noise && fric) launch_pm<true, true>(A, bm, s, st);
-  else if (noise) launch_pm<true, false>(A, bm, s, st);
-  else if (fric) launch_pm<false, true>(A, bm, s, st);
-  else launch_pm<false, false>(A, bm, s, st);
+  if (s.rep_on || s.structural) launch_pm_extra<true>(A, bm, s, st);
+  else launch_pm_extra<false>(A, bm, s, st);
 }
 
 }  // namespace susp

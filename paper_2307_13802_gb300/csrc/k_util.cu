@@ -3,6 +3,8 @@
 // per-block stress and kinetic partial sums into per-replica accumulators.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "device_common.cuh"
 #include "susp_internal.h"
 
@@ -134,8 +136,10 @@ __global__ void k_row_counts(Arrays A, int with_history, long long* __restrict__
   else cnt[p] = A.nnb[cur][p];
 }
 
-// grid (R, 27 + 18): component c of replica r summed over the replica's
-// blocks in a fixed order and added to the running accumulator.
+// grid (R, kPartialLen + kKinLen): component c of replica r summed over the
+// replica's blocks in a fixed order and added to the running accumulator.
+// With a series buffer, the block of the structural xy component also
+// records this sample's Sigma^B_xy = -kT / (shell V) sum w n_x n_y (Eq. 26).
 __global__ void k_reduce_stress(Arrays A, const int* __restrict__ rep_bstart,
                                 int sample_pair, int sample_kin) {
   __shared__ double smem[kBlock / 32];
@@ -171,10 +175,20 @@ __global__ void k_reduce_stress(Arrays A, const int* __restrict__ rep_bstart,
   if (threadIdx.x == 0) res = out[0];
   __syncthreads();
   if (threadIdx.x == 0) {
-    double* acc = A.stress_acc + (int64_t)r * 48;
+    double* acc = A.stress_acc + (int64_t)r * kAccStride;
     acc[c] += res;
-    if (c == 0) acc[45] += 1.0;
-    if (c == kPartialLen) acc[46] += 1.0;
+    if (c == 0) acc[kAccNp] += 1.0;
+    if (c == kPartialLen) acc[kAccNk] += 1.0;
+    if (c == kStrOff + 1 && A.series_cap > 0) {
+      const Replica& R = A.repl[r];
+      long long* cnt = A.series_n + 2 * (int64_t)r;
+      if (cnt[0] < A.series_cap) {
+        A.series[(int64_t)r * A.series_cap + cnt[0]] = -R.kT / A.shell * res / R.V;
+        cnt[0] += 1;
+      } else {
+        cnt[1] += 1;
+      }
+    }
   }
 }
 
@@ -184,6 +198,27 @@ void launch_reduce_stress(const Arrays& A, const BlockMap& bm, int sample_pair,
   if (!sample_pair && !sample_kin) return;
   dim3 grid(A.R, kPartialLen + kKinLen);
   k_reduce_stress<<<grid, kBlock, 0, st>>>(A, A.rep_bstart, sample_pair, sample_kin);
+}
+
+// Green-Kubo autocorrelation (Eq. 33): C[m] = sum_{t < n-m} x[t+m] x[t] / (n-m),
+// one block per lag, each summed in a fixed order.
+__global__ void k_autocorr(const double* __restrict__ x, int64_t n, int64_t max_lag,
+                           double* __restrict__ C) {
+  __shared__ double smem[kBlock / 32];
+  for (int64_t m = blockIdx.x; m < max_lag; m += gridDim.x) {
+    const int64_t cnt = n - m;
+    double acc = 0.0;
+    for (int64_t t = threadIdx.x; t < cnt; t += blockDim.x) acc += x[t + m] * x[t];
+    double v[1] = {acc};
+    double out[1];
+    block_sum_write<1>(v, smem, out);
+    if (threadIdx.x == 0) C[m] = out[0] / (double)cnt;
+  }
+}
+
+void launch_autocorr(const double* x, int64_t n, int64_t max_lag, double* C, cudaStream_t st) {
+  const int64_t grid = std::min<int64_t>(max_lag, 152 * 8);
+  k_autocorr<<<(unsigned)grid, kBlock, 0, st>>>(x, n, max_lag, C);
 }
 
 void launch_load_state(const Arrays& A, const double* x, const double* U,

@@ -32,7 +32,7 @@ constexpr int kNoallocBlocks = SUSP_NOALLOC_MAX_PAIRS / kBlock;
 // header (ticket + padding) then [kNoallocBlocks][27] block partials
 constexpr int kNoallocHeader = 32;
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocHeader +
-                                                          kNoallocBlocks * kPartialLen];
+                                                          kNoallocBlocks * kVirLen];
 
 struct NoallocArgs {
   const double* x;
@@ -52,14 +52,14 @@ struct NoallocArgs {
 template <bool NOISE>
 __global__ void __launch_bounds__(kBlock)
 k_pair_stress_noalloc(NoallocArgs a, double* scratch, double* out) {
-  __shared__ double smem[(kBlock / 32) * kPartialLen];
+  __shared__ double smem[(kBlock / 32) * kVirLen];
   __shared__ bool last;
   unsigned int* ticket = reinterpret_cast<unsigned int*>(scratch);
   double* partial = scratch + kNoallocHeader;
   const int64_t t = blockIdx.x * (int64_t)kBlock + threadIdx.x;
-  double vir[kPartialLen];
+  double vir[kVirLen];
 #pragma unroll
-  for (int q = 0; q < kPartialLen; ++q) vir[q] = 0.0;
+  for (int q = 0; q < kVirLen; ++q) vir[q] = 0.0;
   if (t < a.npairs) {
     // i = lower tag: the pair noise is defined for that orientation
     const int i0 = a.ij[2 * t], j0 = a.ij[2 * t + 1];
@@ -110,7 +110,7 @@ k_pair_stress_noalloc(NoallocArgs a, double* scratch, double* out) {
       }
     }
   }
-  block_sum_write<kPartialLen>(vir, smem, partial + (int64_t)blockIdx.x * kPartialLen);
+  block_sum_write<kVirLen>(vir, smem, partial + (int64_t)blockIdx.x * kVirLen);
   __threadfence();
   if (threadIdx.x == 0) {
     const unsigned int tk = atomicAdd(ticket, 1u);
@@ -119,10 +119,10 @@ k_pair_stress_noalloc(NoallocArgs a, double* scratch, double* out) {
   __syncthreads();
   if (last) {
     __threadfence();
-    for (int c = threadIdx.x; c < kPartialLen; c += blockDim.x) {
+    for (int c = threadIdx.x; c < kVirLen; c += blockDim.x) {
       double s = 0.0;
       for (unsigned int b = 0; b < gridDim.x; ++b)
-        s += *(volatile double*)&partial[(int64_t)b * kPartialLen + c];
+        s += *(volatile double*)&partial[(int64_t)b * kVirLen + c];
       out[c] = s * a.inv_V;
     }
     if (threadIdx.x == 0) *ticket = 0u;

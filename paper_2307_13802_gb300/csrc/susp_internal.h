@@ -30,8 +30,15 @@ namespace susp {
 
 constexpr int kBlock = 256;          // threads per block of particle kernels
 constexpr int kStressComp = 3;       // contact, lubrication, pair Brownian
-constexpr int kPartialLen = 27;      // 3 components x 9 entries
+constexpr int kVirLen = 27;          // their virials: 3 components x 9 entries
+constexpr int kRepOff = 27;          // repulsion virial (9) in a block partial
+constexpr int kStrOff = 36;          // structural sums sum w n n (9), Eq. 26
+constexpr int kPartialLen = 45;      // pair entries of a block partial
 constexpr int kKinLen = 18;          // translational + rotational kinetic
+// per-replica stress accumulator: [0, 45) pair, [45, 63) kinetic, sample counts
+constexpr int kAccStride = 72;
+constexpr int kAccNp = 63;           // pair samples
+constexpr int kAccNk = 64;           // kinetic samples
 
 // error bits of Ctl::err
 constexpr int kErrNonFinite = 1;
@@ -46,6 +53,7 @@ struct Replica {
   double kT;
   double noise_c;    // sqrt(2 kT / dt)
   double eta, kn, kt, mu;
+  double rep_A;      // repulsion scale of Eq. 34 (0: off)
   double V;
   double flip_at;    // 0.5 Lx / Ly
   double flip_by;    // Lx / Ly
@@ -70,7 +78,8 @@ struct Replica {
   float ct_hi, ct_lo;           // current tilt / ncy
   float nt_hi, nt_lo;           // tilt after the next strain advance
   float nct_hi, nct_lo;         // that tilt / ncy
-  float pad1[2];
+  float rep_A_f;
+  float pad1;
 };
 
 // Next strain of the box with the flip of Sec. II.E.
@@ -104,6 +113,7 @@ inline void refresh_constant_fields(Replica& R) {
   R.kn_f = (float)R.kn;
   R.kt_f = (float)R.kt;
   R.mu_f = (float)R.mu;
+  R.rep_A_f = (float)R.rep_A;
   for (int d = 0; d < 3; ++d) {
     R.cwf[d] = (float)(R.L[d] * R.hcell[d]);
     split_df(R.L[d], R.L_hi[d], R.L_lo[d]);
@@ -181,7 +191,11 @@ struct Arrays {
   double* pair_partial; // [nblocks][27]
   float* pair_partial_w; // [nblocks][27] single-precision (mixed path)
   double* kin_partial;  // [nblocks][18]
-  double* stress_acc;   // [R][48]: 27 pair, 18 kinetic, pair / kinetic counts
+  double* stress_acc;   // [R][kAccStride]: 45 pair, 18 kinetic, pair / kinetic counts
+  double* series;       // [R][series_cap] Sigma^B_xy per sampled evaluation
+  long long* series_n;  // [2R]: samples recorded, samples dropped
+  int series_cap;
+  double shell;         // structural shell Delta / a_i
   int* rep_bstart;      // [R + 1] first block of each replica
   Replica* repl;        // [R]
   Ctl* ctl;
@@ -191,14 +205,21 @@ struct StepArgs {
   double dt;
   double hdt;        // dt / 2
   double xi_min, xi_max, skin;
-  double rcmax;      // largest lubrication cutoff (a_i + a_j)(1 + xi_max/2)
+  double rcmax;      // largest interaction range (list cutoff without skin)
   double rate_max;   // largest |rate| over replicas
   double torque_sign;
   int noise, lubrication, onebody, contact, friction;
+  int rep_on;        // some replica has repulsion (Eq. 34)
+  int structural;    // structural Brownian sums (Eq. 26) on sampled steps
+  double rep_fac;    // 1 + 0.01 rep_cut: repulsion range over a_i + a_j
+  double rep_cut;    // repulsion for h <= rep_cut kappa, kappa = 0.01 (a_i + a_j)
+  double rep_hc;     // 0.01 rep_cut: repulsion gap cutoff over a_i + a_j
+  double shell;      // structural shell Delta / a_i
   int advance;       // 1: time advanced since the previous evaluation
   int sample;        // 1: accumulate stresses at this evaluation
   // single-precision copies for the mixed path (set on the host)
   float dt_f, hdt_f, xi_min_f, xi_max_f, tsign_f;
+  float rep_fac_f, rep_hc_f, shell_f;
 };
 
 // ---- host-side launchers (defined in the .cu files) ----------------------
@@ -219,6 +240,8 @@ void launch_finalize_mixed(const Arrays& A, const BlockMap& bm,
 void launch_mirror(const Arrays& A, const BlockMap& bm, cudaStream_t st);
 void launch_pair_mixed(const Arrays& A, const BlockMap& bm, const StepArgs& s,
                        int tpp, cudaStream_t st);
+void launch_autocorr(const double* x, int64_t n, int64_t max_lag, double* C,
+                     cudaStream_t st);
 void launch_reduce_stress(const Arrays& A, const BlockMap& bm, int sample_pair,
                           int sample_kin, cudaStream_t st);
 // neighbour rebuild: `gated` kernels return at once unless ctl->need_rebuild

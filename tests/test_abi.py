@@ -52,3 +52,19 @@ def test_create_without_gpu_fails_cleanly():
     else:
         raise AssertionError("expected SUSP_ENODEV without a GPU")
 
+
+
+def test_green_kubo_argument_errors_need_no_device():
+    import numpy as np
+
+    import paper_2307_13802_gb300 as s
+
+    x = np.zeros(10)
+    for args in ((x, 1, 0.1, 1.0, 1.0), (x, 11, 0.1, 1.0, 1.0), (x, 5, 0.0, 1.0, 1.0),
+                 (x, 5, 0.1, -1.0, 1.0), (x, 5, 0.1, 1.0, 0.0)):
+        try:
+            s.green_kubo(*args)
+        except s.SuspError as e:
+            assert e.code == s.SUSP_EINVAL
+        else:
+            raise AssertionError(f"accepted {args[1:]}")

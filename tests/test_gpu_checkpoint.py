@@ -119,10 +119,10 @@ def test_bad_checkpoint_files_are_reported(tmp_path):
         h.load(str(junk))
     # header: magic, N, R, precision, k, steps, dt, forces_valid, pad
     other = tmp_path / "other.ckpt"
-    other.write_bytes(struct.pack("<8sqiiqqdii", b"SUSPCKP1", 11, 1, 0, 5, 5, 1e-4, 1, 0))
+    other.write_bytes(struct.pack("<8sqiiqqdii", b"SUSPCKP2", 11, 1, 0, 5, 5, 1e-4, 1, 0))
     with pytest.raises(s.SuspError, match="particle or replica count"):
         h.load(str(other))
     short = tmp_path / "short.ckpt"
-    short.write_bytes(struct.pack("<8sqiiqqdii", b"SUSPCKP1", 10, 1, 0, 5, 5, 1e-4, 1, 0))
+    short.write_bytes(struct.pack("<8sqiiqqdii", b"SUSPCKP2", 10, 1, 0, 5, 5, 1e-4, 1, 0))
     with pytest.raises(s.SuspError, match="truncated"):
         h.load(str(short))
