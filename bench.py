@@ -43,7 +43,11 @@ METRIC = "particle-steps/s"
 # (dram__bytes_read.sum + dram__bytes_write.sum), recorded per sphere together
 # with the hash of the source it was taken on; reported only while the
 # source is unchanged.  Filled from profiles/.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # ncu --set full, k_pair_mixed<1,1,1,0>, 1M bench workload: 298.3 MB read +
+    # 96.3 MB written per launch (profiles/k_pair_mixed_1M.md)
+    "k_pair_mixed": {"bytes_per_sphere": 394.633, "source_sha": "26bb127685e8aeba"},
+}
 
 
 def _src_hash(name: str) -> str:

@@ -186,6 +186,26 @@ int susp_get_forces(susp_t* h, double* F, double* T);
  * automatically by the step when the displacement bound exceeds the skin. */
 int susp_build_neighbors(susp_t* h);
 
+/* Sets the neighbour-list skin (length units, >= 0): the cell grid is laid
+ * out again for the new list cutoff and the list is rebuilt before the next
+ * evaluation.  SUSP_EINVAL if a box then holds fewer than 3 cells along an
+ * axis.  Batch handles: one skin for all replicas. */
+int susp_set_skin(susp_t* h, double skin);
+
+/* Autotuner: for each candidate skin[c] (c < n) advances trial_steps steps
+ * of size dt from the current state (after an untimed pass of up to 64
+ * steps that captures the graphs), times them with CUDA events on the
+ * handle's stream and writes the device milliseconds per step to
+ * ms_per_step[c] (NaN where the skin is not possible; the array may be
+ * NULL).  The fastest skin is kept and written to *chosen, and the state,
+ * forces, tangential history, clock and stress sums are put back as they
+ * were, so tuning leaves the run unchanged.  The cell size follows from the
+ * skin (cells are one list cutoff thick); the pair kernels map one list
+ * item per lane whatever the row lengths, so there is no threads-per-
+ * particle choice to make. */
+int susp_autotune(susp_t* h, int64_t trial_steps, double dt, const double* skins,
+                  int32_t n, double* ms_per_step, double* chosen);
+
 /* Evaluates forces, torques and pair stresses at the current state without
  * advancing time (tangential history is not incremented). */
 int susp_evaluate(susp_t* h);

@@ -91,6 +91,8 @@ _SIGNATURES = {
     "susp_get_series": (C.c_int, [_H, C.c_int32, _D, C.c_int64, _I64, _I64]),
     "susp_green_kubo": (C.c_int, [_D, C.c_int64, C.c_int64, C.c_double, C.c_double,
                                   C.c_double, _D, _D, _D]),
+    "susp_set_skin": (C.c_int, [_H, C.c_double]),
+    "susp_autotune": (C.c_int, [_H, C.c_int64, C.c_double, _D, C.c_int32, _D, _D]),
     "susp_save": (C.c_int, [_H, C.c_char_p]),
     "susp_load": (C.c_int, [_H, C.c_char_p]),
 }
@@ -297,6 +299,20 @@ class System:
                 "threads_per_particle", "precision", "replicas", "N",
                 "graph_steps", "device_bytes", "launches")
         return dict(zip(keys, out.tolist()))
+
+    def set_skin(self, skin: float):
+        self._chk(lib.susp_set_skin(self._h, float(skin)))
+
+    def autotune(self, trial_steps: int, dt: float, skins):
+        """Times trial_steps steps at each candidate skin from the current
+        state, keeps the fastest and restores the state; returns
+        (chosen skin, ms per step of each candidate)."""
+        sk = np.ascontiguousarray(skins, dtype=np.float64)
+        ms = np.zeros(len(sk))
+        chosen = C.c_double(0.0)
+        self._chk(lib.susp_autotune(self._h, int(trial_steps), float(dt), _dp(sk), len(sk),
+                                    _dp(ms), C.byref(chosen)))
+        return chosen.value, ms
 
     def save(self, path: str):
         self._chk(lib.susp_save(self._h, path.encode()))

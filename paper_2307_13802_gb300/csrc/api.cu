@@ -49,6 +49,7 @@ struct susp_s {
   double rcmax = 0.0;
   double amax = 0.0;
   int64_t ncell = 0;
+  int64_t ncell_cap = 0;   // cells the cell arrays hold (the layout of skin 0)
   // block map (host + device)
   std::vector<int> bm_rep, bm_start, bm_end, rep_bstart;
   BlockMap bm{};
@@ -92,6 +93,8 @@ struct susp_s {
 };
 
 namespace {
+
+int64_t layout_cells(std::vector<Replica>& reps, double rlist, std::string& msg);
 
 int fail(susp_t* h, int code, const std::string& msg) {
   if (h) h->err = msg;
@@ -221,10 +224,7 @@ int common_create(susp_t** out, int32_t R, const int64_t* N_r,
     if (p_r[0].structural) rc = std::max(rc, S + p_r[0].shell * h->amax);
     h->rcmax = rc;
   }
-  const double rlist = h->rcmax + p_r[0].skin;
-  const double guard = rlist * (1.0 + 1e-9) + 1e-12;
   h->repl_h.resize(R);
-  int64_t cell_base = 0;
   for (int r = 0; r < R; ++r) {
     Replica& Rr = h->repl_h[r];
     std::memset(&Rr, 0, sizeof(Rr));
@@ -236,37 +236,27 @@ int common_create(susp_t** out, int32_t R, const int64_t* N_r,
     }
     fill_replica_physics(Rr, p_r[r]);
     Rr.V = Rr.L[0] * Rr.L[1] * Rr.L[2];
+    for (int d = 0; d < 3; ++d) Rr.iL[d] = 1.0 / Rr.L[d];
     Rr.flip_at = 0.5 * Rr.L[0] / Rr.L[1];
     Rr.flip_by = Rr.L[0] / Rr.L[1];
     Rr.strain = 0.0;
     Rr.tilt = 0.0;
-    // cell thickness along x for the largest tilt Lx/2
-    const double tmax = 0.5 * Rr.L[0];
-    const double wx = Rr.L[0] * Rr.L[1] / std::sqrt(Rr.L[1] * Rr.L[1] + tmax * tmax);
-    Rr.nc[0] = (int)std::floor(wx / guard);
-    Rr.nc[1] = (int)std::floor(Rr.L[1] / guard);
-    Rr.nc[2] = (int)std::floor(Rr.L[2] / guard);
-    if (Rr.nc[0] > 1023 || Rr.nc[1] > 1023 || Rr.nc[2] > 1023) {
-      delete h;
-      g_create_error = "more than 1023 cells along a box edge";
-      return SUSP_EINVAL;
-    }
-    if (Rr.nc[0] < 3 || Rr.nc[1] < 3 || Rr.nc[2] < 3) {
-      delete h;
-      char buf[256];
-      std::snprintf(buf, sizeof buf,
-                    "replica %d: box (%g, %g, %g) holds fewer than 3 cells of the "
-                    "list cutoff %g along some axis", r, Rr.L[0], Rr.L[1], Rr.L[2], rlist);
-      g_create_error = buf;
-      return SUSP_EINVAL;
-    }
-    for (int d = 0; d < 3; ++d) Rr.hcell[d] = 1.0 / Rr.nc[d];
-    Rr.cell_base = cell_base;
-    cell_base += (int64_t)Rr.nc[0] * Rr.nc[1] * Rr.nc[2];
     Rr.p0 = h->off[r];
     Rr.n = N_r[r];
   }
-  h->ncell = cell_base;
+  std::string cmsg;
+  h->ncell = layout_cells(h->repl_h, h->rcmax + p_r[0].skin, cmsg);
+  if (h->ncell < 0) {
+    delete h;
+    g_create_error = cmsg;
+    return SUSP_EINVAL;
+  }
+  // the cell arrays are sized for the finest grid any skin >= 0 can ask for
+  {
+    std::vector<Replica> fine = h->repl_h;
+    const int64_t nf = layout_cells(fine, h->rcmax, cmsg);
+    h->ncell_cap = std::max<int64_t>(h->ncell, nf);
+  }
   // block map: blocks never straddle replicas
   h->rep_bstart.push_back(0);
   for (int r = 0; r < R; ++r) {
@@ -353,10 +343,10 @@ int allocate(susp_t* h) {
   ok &= alloc_n(h, &A.cell, Np);
   ok &= alloc_n(h, &A.key, Np);
   ok &= alloc_n(h, &A.perm, Np);
-  ok &= alloc_n(h, &A.cell_count, h->ncell + 1);
-  ok &= alloc_n(h, &A.cell_start, h->ncell + 1);
-  ok &= alloc_n(h, &A.cell_fill, h->ncell + 1);
-  const int64_t nparts = (h->ncell + kBlock * 8 - 1) / (kBlock * 8);
+  ok &= alloc_n(h, &A.cell_count, h->ncell_cap + 1);
+  ok &= alloc_n(h, &A.cell_start, h->ncell_cap + 1);
+  ok &= alloc_n(h, &A.cell_fill, h->ncell_cap + 1);
+  const int64_t nparts = (h->ncell_cap + kBlock * 8 - 1) / (kBlock * 8);
   ok &= alloc_n(h, &A.scan_part, nparts + 1);
   const int nb = (int)h->bm_rep.size();
   ok &= alloc_n(h, &A.pair_partial, (int64_t)nb * kPartialLen);
@@ -848,129 +838,100 @@ struct FileCloser {
   ~FileCloser() { if (f) std::fclose(f); }
 };
 
-int save_checkpoint(susp_t* h, const char* path) {
-  const int64_t N = h->N;
-  std::vector<double> st(15 * N);
-  int rc = SUSP_OK;
-  for (int w = 0; w < 5 && !rc; ++w) rc = gather_host(h, w, st.data() + 3 * N * w);
-  if (rc) return rc;
+// The whole resumable state of a handle on the host (the checkpoint body).
+struct Snapshot {
+  CkHeader hd{};
+  std::vector<susp_params> pr;
+  std::vector<double> strain, st, acc;  // st: x, U, Omega, F, T [N][3] each
+  std::vector<int32_t> ij;              // touching pairs with history
+  std::vector<double> xi;
   int64_t np = 0;
-  rc = list_pairs(h, 1, nullptr, nullptr, 0, &np);
+};
+
+int take_snapshot(susp_t* h, Snapshot& sn) {
+  const int64_t N = h->N;
+  sn.st.assign(15 * N, 0.0);
+  int rc = SUSP_OK;
+  for (int w = 0; w < 5 && !rc; ++w) rc = gather_host(h, w, sn.st.data() + 3 * N * w);
   if (rc) return rc;
-  std::vector<int32_t> ij(2 * std::max<int64_t>(np, 1));
-  std::vector<double> xi(3 * std::max<int64_t>(np, 1));
-  if (np > 0) {
+  rc = list_pairs(h, 1, nullptr, nullptr, 0, &sn.np);
+  if (rc) return rc;
+  sn.ij.assign(2 * std::max<int64_t>(sn.np, 1), 0);
+  sn.xi.assign(3 * std::max<int64_t>(sn.np, 1), 0.0);
+  if (sn.np > 0) {
     int64_t np2 = 0;
-    rc = list_pairs(h, 1, ij.data(), xi.data(), np, &np2);
+    rc = list_pairs(h, 1, sn.ij.data(), sn.xi.data(), sn.np, &np2);
     if (rc) return rc;
   }
   Ctl c{};
   std::vector<Replica> rep(h->R);
-  std::vector<double> acc(kAccStride * (size_t)h->R);
+  sn.acc.assign(kAccStride * (size_t)h->R, 0.0);
   CK(cudaMemcpyAsync(&c, h->A.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(rep.data(), h->A.repl, sizeof(Replica) * h->R, cudaMemcpyDeviceToHost,
                      h->stream));
-  CK(cudaMemcpyAsync(acc.data(), h->A.stress_acc, sizeof(double) * acc.size(),
+  CK(cudaMemcpyAsync(sn.acc.data(), h->A.stress_acc, sizeof(double) * sn.acc.size(),
                      cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  CkHeader hd{};
-  std::memcpy(hd.magic, kCkMagic, 8);
-  hd.N = N;
-  hd.R = h->R;
-  hd.precision = h->p0.precision;
-  hd.k = c.k;
-  hd.steps_done = h->steps_done;
-  hd.last_dt = h->last_dt;
-  hd.forces_valid = h->forces_valid ? 1 : 0;
-  std::vector<double> strain(h->R);
-  for (int r = 0; r < h->R; ++r) strain[r] = rep[r].strain;
-  FileCloser fc{std::fopen(path, "wb")};
-  if (!fc.f) return fail(h, SUSP_EINVAL, std::string("cannot open ") + path + " for writing");
-  bool ok = std::fwrite(&hd, sizeof hd, 1, fc.f) == 1;
-  ok = ok && std::fwrite(h->pr.data(), sizeof(susp_params), h->R, fc.f) == (size_t)h->R;
-  ok = ok && std::fwrite(strain.data(), sizeof(double), h->R, fc.f) == (size_t)h->R;
-  ok = ok && std::fwrite(h->radii.data(), sizeof(double), N, fc.f) == (size_t)N;
-  ok = ok && std::fwrite(st.data(), sizeof(double), st.size(), fc.f) == st.size();
-  ok = ok && std::fwrite(acc.data(), sizeof(double), acc.size(), fc.f) == acc.size();
-  ok = ok && std::fwrite(&np, sizeof np, 1, fc.f) == 1;
-  ok = ok && std::fwrite(ij.data(), sizeof(int32_t), 2 * np, fc.f) == (size_t)(2 * np);
-  ok = ok && std::fwrite(xi.data(), sizeof(double), 3 * np, fc.f) == (size_t)(3 * np);
-  ok = ok && std::fwrite(kCkEnd, 1, 8, fc.f) == 8;
-  ok = (std::fflush(fc.f) == 0) && ok;
-  if (!ok) return fail(h, SUSP_EINVAL, std::string("write to ") + path + " failed");
+  std::memcpy(sn.hd.magic, kCkMagic, 8);
+  sn.hd.N = N;
+  sn.hd.R = h->R;
+  sn.hd.precision = h->p0.precision;
+  sn.hd.k = c.k;
+  sn.hd.steps_done = h->steps_done;
+  sn.hd.last_dt = h->last_dt;
+  sn.hd.forces_valid = h->forces_valid ? 1 : 0;
+  sn.pr = h->pr;
+  sn.strain.resize(h->R);
+  for (int r = 0; r < h->R; ++r) sn.strain[r] = rep[r].strain;
   return SUSP_OK;
 }
 
-int load_checkpoint(susp_t* h, const char* path) {
-  FileCloser fc{std::fopen(path, "rb")};
-  if (!fc.f) return fail(h, SUSP_EINVAL, std::string("cannot open ") + path);
-  auto bad = [&](const char* what) {
-    return fail(h, SUSP_EINVAL, std::string("checkpoint ") + path + ": " + what);
-  };
-  CkHeader hd{};
-  if (std::fread(&hd, sizeof hd, 1, fc.f) != 1 || std::memcmp(hd.magic, kCkMagic, 8) != 0)
-    return bad("not a checkpoint of this library");
-  if (hd.N != h->N || hd.R != h->R) return bad("particle or replica count differs from the handle");
-  if (hd.precision != h->p0.precision) return bad("precision differs from the handle");
+// Puts a snapshot (already checked against the handle's sizes, radii and
+// parameters) back on the device.  `what` names the source in messages.
+int restore_snapshot(susp_t* h, const Snapshot& sn, const std::string& what) {
+  auto bad = [&](const char* why) { return fail(h, SUSP_EINVAL, what + ": " + why); };
   const int64_t N = h->N;
-  std::vector<susp_params> pr(h->R);
-  std::vector<double> strain(h->R), radii(N), st(15 * N), acc(kAccStride * (size_t)h->R);
-  if (std::fread(pr.data(), sizeof(susp_params), h->R, fc.f) != (size_t)h->R ||
-      std::fread(strain.data(), sizeof(double), h->R, fc.f) != (size_t)h->R ||
-      std::fread(radii.data(), sizeof(double), N, fc.f) != (size_t)N ||
-      std::fread(st.data(), sizeof(double), st.size(), fc.f) != st.size() ||
-      std::fread(acc.data(), sizeof(double), acc.size(), fc.f) != acc.size())
-    return bad("truncated");
-  for (int r = 0; r < h->R; ++r)
-    if (!same_static_params(pr[r], h->pr[r])) return bad("model parameters differ from the handle");
-  if (std::memcmp(radii.data(), h->radii.data(), sizeof(double) * N) != 0)
-    return bad("radii differ from the handle");
-  int64_t np = 0;
-  if (std::fread(&np, sizeof np, 1, fc.f) != 1 || np < 0 || np > 64 * N) return bad("truncated");
-  std::vector<int32_t> ij(2 * std::max<int64_t>(np, 1));
-  std::vector<double> xi(3 * std::max<int64_t>(np, 1));
-  char end[8];
-  if (std::fread(ij.data(), sizeof(int32_t), 2 * np, fc.f) != (size_t)(2 * np) ||
-      std::fread(xi.data(), sizeof(double), 3 * np, fc.f) != (size_t)(3 * np) ||
-      std::fread(end, 1, 8, fc.f) != 8 || std::memcmp(end, kCkEnd, 8) != 0)
-    return bad("truncated");
   // history rows (tag order): partners of each lower tag
   std::vector<int> rowlen(N, 0);
-  for (int64_t e = 0; e < np; ++e) {
-    const int32_t i = ij[2 * e], j = ij[2 * e + 1];
+  for (int64_t e = 0; e < sn.np; ++e) {
+    const int32_t i = sn.ij[2 * e], j = sn.ij[2 * e + 1];
     if (i < 0 || j < 0 || i >= N || j >= N || i == j || h->rep_of[i] != h->rep_of[j])
       return bad("history pair out of range");
     if (++rowlen[i] > std::min(h->kmax, 64)) return bad("more touching pairs per sphere than kmax");
   }
-  // the file is consistent with the handle: from here on the device is used
+  for (int r = 0; r < h->R; ++r)
+    if (!(std::fabs(sn.strain[r]) <= h->repl_h[r].flip_at)) return bad("strain out of range");
+  // consistent with the handle: from here on the device is used
   CK(cudaSetDevice(h->dev));
   int rc = allocate(h);
   if (rc) return rc;
   // clock first, so that the state is wrapped in the saved box
   for (int r = 0; r < h->R; ++r) {
     Replica& R = h->repl_h[r];
-    if (!(std::fabs(strain[r]) <= R.flip_at)) return bad("strain out of range");
-    R.strain = strain[r];
-    R.tilt = strain[r] * R.L[1];
-    R.rate = pr[r].shear_rate;
-    R.kT = pr[r].kT;
-    R.key0 = (uint32_t)(pr[r].seed & 0xffffffffull);
-    R.key1 = (uint32_t)(pr[r].seed >> 32);
-    h->pr[r].shear_rate = pr[r].shear_rate;
-    h->pr[r].kT = pr[r].kT;
-    h->pr[r].seed = pr[r].seed;
-    h->pr[r].dt = pr[r].dt;
+    R.strain = sn.strain[r];
+    R.tilt = sn.strain[r] * R.L[1];
+    R.rate = sn.pr[r].shear_rate;
+    R.kT = sn.pr[r].kT;
+    R.key0 = (uint32_t)(sn.pr[r].seed & 0xffffffffull);
+    R.key1 = (uint32_t)(sn.pr[r].seed >> 32);
+    h->pr[r].shear_rate = sn.pr[r].shear_rate;
+    h->pr[r].kT = sn.pr[r].kT;
+    h->pr[r].seed = sn.pr[r].seed;
+    h->pr[r].dt = sn.pr[r].dt;
     refresh_strain_fields(R);
   }
   CK(cudaMemcpyAsync(h->A.repl, h->repl_h.data(), sizeof(Replica) * h->R,
                      cudaMemcpyHostToDevice, h->stream));
-  drop_graphs(h);
-  if (hd.last_dt > 0) h->last_dt = hd.last_dt;
-  rc = set_state_impl(h, st.data(), st.data() + 3 * N, st.data() + 6 * N, cudaMemcpyHostToDevice);
+  // captured graphs read the state and the replica table from device
+  // memory, so they stay valid unless the timestep changes
+  if (sn.hd.last_dt > 0 && sn.hd.last_dt != h->last_dt) drop_graphs(h);
+  if (sn.hd.last_dt > 0) h->last_dt = sn.hd.last_dt;
+  const double* st = sn.st.data();
+  rc = set_state_impl(h, st, st + 3 * N, st + 6 * N, cudaMemcpyHostToDevice);
   if (rc) return rc;
-  long long kk = (long long)hd.k;
+  long long kk = (long long)sn.hd.k;
   CK(cudaMemcpyAsync(&h->A.ctl->k, &kk, sizeof kk, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(h->A.stress_acc, acc.data(), sizeof(double) * acc.size(),
+  CK(cudaMemcpyAsync(h->A.stress_acc, sn.acc.data(), sizeof(double) * sn.acc.size(),
                      cudaMemcpyHostToDevice, h->stream));
   Ctl c{};
   CK(cudaMemcpyAsync(&c, h->A.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
@@ -980,8 +941,8 @@ int load_checkpoint(susp_t* h, const char* path) {
   const bool mixed = h->p0.precision == SUSP_MIXED;
   // forces and torques of the last evaluation, in the tag order the state
   // was just loaded in; the rebuild below permutes them with the state
-  const double* F = st.data() + 9 * N;
-  const double* T = st.data() + 12 * N;
+  const double* F = st + 9 * N;
+  const double* T = st + 12 * N;
   if (mixed) {
     std::vector<float> f4(4 * N), t4(4 * N);
     for (int64_t p = 0; p < N; ++p)
@@ -1002,18 +963,18 @@ int load_checkpoint(susp_t* h, const char* path) {
   }
   // the saved history as the live list: the rebuild carries it into the new
   // list by (tag_i, tag_j) as it does for any rebuild
-  if (np > 0) {
+  if (sn.np > 0) {
     const int m = *std::max_element(rowlen.begin(), rowlen.end());
     std::vector<int> nbr((size_t)m * N, 0), fill(N, 0);
     std::vector<double> hv((size_t)3 * m * N, 0.0);
     std::vector<unsigned long long> cm(N, 0ull);
-    for (int64_t e = 0; e < np; ++e) {
-      const int32_t i = ij[2 * e], j = ij[2 * e + 1];
+    for (int64_t e = 0; e < sn.np; ++e) {
+      const int32_t i = sn.ij[2 * e], j = sn.ij[2 * e + 1];
       const int sl = fill[i]++;
       nbr[(size_t)sl * N + i] = j;
       cm[i] |= 1ull << sl;
       for (int q = 0; q < 3; ++q) {
-        const double v = xi[3 * e + q];
+        const double v = sn.xi[3 * e + q];
         double& slot = hv[((size_t)q * m + sl) * N + i];
         if (mixed) {
           const float hi = (float)v;
@@ -1040,9 +1001,143 @@ int load_checkpoint(susp_t* h, const char* path) {
   StepArgs s = make_args(h, h->last_dt > 0 ? h->last_dt : h->p0.dt, 0, 0);
   launch_request_rebuild(h->A, h->stream);
   launch_rebuild(h->A, h->bm, s, h->stream, mixed);
-  h->steps_done = hd.steps_done;
-  h->forces_valid = hd.forces_valid != 0;
+  h->steps_done = sn.hd.steps_done;
+  h->forces_valid = sn.hd.forces_valid != 0;
   return check_errors(h);
+}
+
+int save_checkpoint(susp_t* h, const char* path) {
+  Snapshot sn;
+  int rc = take_snapshot(h, sn);
+  if (rc) return rc;
+  const int64_t N = h->N;
+  FileCloser fc{std::fopen(path, "wb")};
+  if (!fc.f) return fail(h, SUSP_EINVAL, std::string("cannot open ") + path + " for writing");
+  bool ok = std::fwrite(&sn.hd, sizeof sn.hd, 1, fc.f) == 1;
+  ok = ok && std::fwrite(sn.pr.data(), sizeof(susp_params), h->R, fc.f) == (size_t)h->R;
+  ok = ok && std::fwrite(sn.strain.data(), sizeof(double), h->R, fc.f) == (size_t)h->R;
+  ok = ok && std::fwrite(h->radii.data(), sizeof(double), N, fc.f) == (size_t)N;
+  ok = ok && std::fwrite(sn.st.data(), sizeof(double), sn.st.size(), fc.f) == sn.st.size();
+  ok = ok && std::fwrite(sn.acc.data(), sizeof(double), sn.acc.size(), fc.f) == sn.acc.size();
+  ok = ok && std::fwrite(&sn.np, sizeof sn.np, 1, fc.f) == 1;
+  ok = ok && std::fwrite(sn.ij.data(), sizeof(int32_t), 2 * sn.np, fc.f) == (size_t)(2 * sn.np);
+  ok = ok && std::fwrite(sn.xi.data(), sizeof(double), 3 * sn.np, fc.f) == (size_t)(3 * sn.np);
+  ok = ok && std::fwrite(kCkEnd, 1, 8, fc.f) == 8;
+  ok = (std::fflush(fc.f) == 0) && ok;
+  if (!ok) return fail(h, SUSP_EINVAL, std::string("write to ") + path + " failed");
+  return SUSP_OK;
+}
+
+int load_checkpoint(susp_t* h, const char* path) {
+  FileCloser fc{std::fopen(path, "rb")};
+  if (!fc.f) return fail(h, SUSP_EINVAL, std::string("cannot open ") + path);
+  const std::string what = std::string("checkpoint ") + path;
+  auto bad = [&](const char* why) { return fail(h, SUSP_EINVAL, what + ": " + why); };
+  Snapshot sn;
+  if (std::fread(&sn.hd, sizeof sn.hd, 1, fc.f) != 1 || std::memcmp(sn.hd.magic, kCkMagic, 8) != 0)
+    return bad("not a checkpoint of this library");
+  if (sn.hd.N != h->N || sn.hd.R != h->R)
+    return bad("particle or replica count differs from the handle");
+  if (sn.hd.precision != h->p0.precision) return bad("precision differs from the handle");
+  const int64_t N = h->N;
+  sn.pr.resize(h->R);
+  sn.strain.resize(h->R);
+  sn.st.resize(15 * N);
+  sn.acc.resize(kAccStride * (size_t)h->R);
+  std::vector<double> radii(N);
+  if (std::fread(sn.pr.data(), sizeof(susp_params), h->R, fc.f) != (size_t)h->R ||
+      std::fread(sn.strain.data(), sizeof(double), h->R, fc.f) != (size_t)h->R ||
+      std::fread(radii.data(), sizeof(double), N, fc.f) != (size_t)N ||
+      std::fread(sn.st.data(), sizeof(double), sn.st.size(), fc.f) != sn.st.size() ||
+      std::fread(sn.acc.data(), sizeof(double), sn.acc.size(), fc.f) != sn.acc.size())
+    return bad("truncated");
+  for (int r = 0; r < h->R; ++r)
+    if (!same_static_params(sn.pr[r], h->pr[r])) return bad("model parameters differ from the handle");
+  if (std::memcmp(radii.data(), h->radii.data(), sizeof(double) * N) != 0)
+    return bad("radii differ from the handle");
+  if (std::fread(&sn.np, sizeof sn.np, 1, fc.f) != 1 || sn.np < 0 || sn.np > 64 * N)
+    return bad("truncated");
+  sn.ij.resize(2 * std::max<int64_t>(sn.np, 1));
+  sn.xi.resize(3 * std::max<int64_t>(sn.np, 1));
+  char end[8];
+  if (std::fread(sn.ij.data(), sizeof(int32_t), 2 * sn.np, fc.f) != (size_t)(2 * sn.np) ||
+      std::fread(sn.xi.data(), sizeof(double), 3 * sn.np, fc.f) != (size_t)(3 * sn.np) ||
+      std::fread(end, 1, 8, fc.f) != 8 || std::memcmp(end, kCkEnd, 8) != 0)
+    return bad("truncated");
+  return restore_snapshot(h, sn, what);
+}
+
+// ---------------------------------------------------------------------------
+// cell layout, skin and the autotuner
+// ---------------------------------------------------------------------------
+// Cell grid of every replica for list cutoff rlist: nc cells per axis, each
+// at least rlist thick for any tilt |tilt| <= Lx/2 (so two spheres closer
+// than rlist sit in the same or adjacent cells).  Fills nc, hcell and
+// cell_base; returns the total cell count, or -1 with a message.
+int64_t layout_cells(std::vector<Replica>& reps, double rlist, std::string& msg) {
+  const double guard = rlist * (1.0 + 1e-9) + 1e-12;
+  int64_t base = 0;
+  for (size_t r = 0; r < reps.size(); ++r) {
+    Replica& Rr = reps[r];
+    const double tmax = 0.5 * Rr.L[0];
+    const double wx = Rr.L[0] * Rr.L[1] / std::sqrt(Rr.L[1] * Rr.L[1] + tmax * tmax);
+    const int nc[3] = {(int)std::floor(wx / guard), (int)std::floor(Rr.L[1] / guard),
+                       (int)std::floor(Rr.L[2] / guard)};
+    if (nc[0] > 1023 || nc[1] > 1023 || nc[2] > 1023) {
+      msg = "more than 1023 cells along a box edge";
+      return -1;
+    }
+    if (nc[0] < 3 || nc[1] < 3 || nc[2] < 3) {
+      char buf[256];
+      std::snprintf(buf, sizeof buf,
+                    "replica %d: box (%g, %g, %g) holds fewer than 3 cells of the "
+                    "list cutoff %g along some axis", (int)r, Rr.L[0], Rr.L[1], Rr.L[2], rlist);
+      msg = buf;
+      return -1;
+    }
+    for (int d = 0; d < 3; ++d) {
+      Rr.nc[d] = nc[d];
+      Rr.hcell[d] = 1.0 / nc[d];
+    }
+    Rr.cell_base = base;
+    base += (int64_t)nc[0] * nc[1] * nc[2];
+  }
+  return base;
+}
+
+int set_skin_impl(susp_t* h, double skin) {
+  if (!(skin >= 0) || !std::isfinite(skin)) return fail(h, SUSP_EINVAL, "skin must be >= 0");
+  std::vector<Replica> trial = h->repl_h;
+  std::string msg;
+  const int64_t nc = layout_cells(trial, h->rcmax + skin, msg);
+  if (nc < 0) return fail(h, SUSP_EINVAL, msg);
+  if (nc > h->ncell_cap) return fail(h, SUSP_EINVAL, "skin too small for the cell arrays");
+  if (h->allocated) {
+    int rc = sync_replicas(h, h->last_dt);  // current strains
+    if (rc) return rc;
+  }
+  for (int r = 0; r < h->R; ++r) {
+    Replica& R = h->repl_h[r];
+    for (int d = 0; d < 3; ++d) {
+      R.nc[d] = trial[r].nc[d];
+      R.hcell[d] = trial[r].hcell[d];
+    }
+    R.cell_base = trial[r].cell_base;
+    refresh_constant_fields(R);
+    refresh_strain_fields(R);
+    h->pr[r].skin = skin;
+  }
+  h->p0.skin = skin;
+  h->ncell = nc;
+  h->A.ncell = nc;
+  drop_graphs(h);
+  if (h->allocated) {
+    CK(cudaMemcpyAsync(h->A.repl, h->repl_h.data(), sizeof(Replica) * h->R,
+                       cudaMemcpyHostToDevice, h->stream));
+    launch_request_rebuild(h->A, h->stream);
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return SUSP_OK;
 }
 
 }  // namespace
@@ -1438,6 +1533,70 @@ int susp_get_info(susp_t* h, double* info) {
   info[5] = r0.strain;
   info[6] = r0.tilt;
   return SUSP_OK;
+}
+
+int susp_set_skin(susp_t* h, double skin) {
+  if (!h) return SUSP_EINVAL;
+  h->err.clear();
+  return set_skin_impl(h, skin);
+}
+
+int susp_autotune(susp_t* h, int64_t trial_steps, double dt, const double* skins, int32_t n,
+                  double* ms_per_step, double* chosen) {
+  if (!h) return SUSP_EINVAL;
+  h->err.clear();
+  if (!skins || n < 1 || !chosen) return fail(h, SUSP_EINVAL, "need skins[n], n >= 1, chosen");
+  if (trial_steps < 1) return fail(h, SUSP_EINVAL, "trial_steps must be >= 1");
+  if (!(dt > 0)) return fail(h, SUSP_EINVAL, "dt must be > 0");
+  if (!h->have_state) return fail(h, SUSP_ESTATE, "susp_set_state() must come first");
+  CK(cudaSetDevice(h->dev));
+  const double skin0 = h->p0.skin;
+  Snapshot sn;
+  int rc = take_snapshot(h, sn);
+  if (rc) return rc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best_ms = -1.0, best = skin0;
+  for (int c = 0; c < n; ++c) {
+    double ms = std::nan("");
+    if (set_skin_impl(h, skins[c]) == SUSP_OK) {
+      // one untimed pass (graph capture, first rebuild), then the timed
+      // trial from the same state
+      rc = restore_snapshot(h, sn, "autotune");
+      if (!rc) rc = run_steps(h, std::min<int64_t>(trial_steps, 64), dt);
+      if (!rc) rc = restore_snapshot(h, sn, "autotune");
+      if (!rc) {
+        cudaEventRecord(e0, h->stream);
+        rc = run_steps(h, trial_steps, dt);
+        cudaEventRecord(e1, h->stream);
+      }
+      if (!rc) {
+        float t = 0.f;
+        if (cudaEventSynchronize(e1) == cudaSuccess &&
+            cudaEventElapsedTime(&t, e0, e1) == cudaSuccess)
+          ms = (double)t / (double)trial_steps;
+      }
+      if (rc) break;
+    }
+    h->err.clear();
+    if (ms_per_step) ms_per_step[c] = ms;
+    if (ms == ms && (best_ms < 0.0 || ms < best_ms)) {
+      best_ms = ms;
+      best = skins[c];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) {
+    set_skin_impl(h, skin0);
+    restore_snapshot(h, sn, "autotune");
+    return rc;
+  }
+  rc = set_skin_impl(h, best);
+  if (!rc) rc = restore_snapshot(h, sn, "autotune");
+  *chosen = best;
+  return rc;
 }
 
 int susp_save(susp_t* h, const char* path) {

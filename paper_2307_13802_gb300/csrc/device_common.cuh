@@ -192,16 +192,22 @@ __device__ __forceinline__ void history_update(double* xt, const double* n,
 }
 
 // Minimum image of x_q - x_p in the sliding-brick form of the tilted box:
-// the y image count sy first (shifting x by sy * tilt), then x and z.
+// the y image count sy first (shifting x by sy * tilt), then x and z.  The
+// image counts are rounded from products with the reciprocal edges iL
+// rather than quotients: the two differ only where a coordinate difference
+// is within an ulp of half an edge (plus whole edges), and a pair closer
+// than a third of every edge -- every pair any kernel uses, since boxes hold
+// at least three list cutoffs -- has differences at least a sixth of an edge
+// away from those points, so its counts, and r, are the same either way.
 __device__ __forceinline__ void min_image_f64(double dx, double dy, double dz,
-                                              const double* L, double tilt,
-                                              double* r, double* sy_out) {
-  const double sy = rint(dy / L[1]);
+                                              const double* L, const double* iL,
+                                              double tilt, double* r, double* sy_out) {
+  const double sy = rint(dy * iL[1]);
   dy = dy - sy * L[1];
   dx = dx - sy * tilt;
-  const double sx = rint(dx / L[0]);
+  const double sx = rint(dx * iL[0]);
   dx = dx - sx * L[0];
-  const double sz = rint(dz / L[2]);
+  const double sz = rint(dz * iL[2]);
   dz = dz - sz * L[2];
   r[0] = dx; r[1] = dy; r[2] = dz;
   *sy_out = sy;

@@ -224,9 +224,6 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Arrays A, StepArgs s, dou
   if (p >= A.N) return;
   const int r = A.rep[nxt][p];
   const Replica& R = A.repl[r];
-  const double L[3] = {R.L[0], R.L[1], R.L[2]};
-  const double tilt = R.tilt;
-  const double4_32a P = read_rec_d(A.pos[nxt], A.mixed, p);
   const int local = (int)(A.cell[p] - R.cell_base);
   const int ncx = R.nc[0], ncy = R.nc[1], ncz = R.nc[2];
   const int cx = local % ncx, cy = (local / ncx) % ncy, cz = local / (ncx * ncy);
@@ -234,35 +231,82 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Arrays A, StepArgs s, dou
   int* row = A.nbr[nxt] + p;
   int cnt = 0;
   const int kmax = A.kmax;
-  for (int dz = -1; dz <= 1; ++dz) {
-    const int zz = (cz + dz + ncz) % ncz;
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int yy = (cy + dy + ncy) % ncy;
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int xx = (cx + dx + ncx) % ncx;
-        const int64_t key = R.cell_base + ((int64_t)zz * ncy + yy) * ncx + xx;
-        const int q0 = A.cell_start[key], q1 = A.cell_start[key + 1];
-        for (int q = q0; q < q1; ++q) {
-          if (q <= p) continue;
-          const double4_32a Q = read_rec_d(A.pos[nxt], A.mixed, q);
-          double rr[3], sy;
-          min_image_f64(Q.x - P.x, Q.y - P.y, Q.z - P.z, L, tilt, rr, &sy);
-          const double d2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
-          // widest interaction range of the pair (lubrication cutoff,
-          // repulsion range, structural shell), then the skin
-          double rc = (P.w + Q.w) * rc_fac;
-          if (s.rep_on) {
-            const double rr = (P.w + Q.w) * s.rep_fac;
-            if (rr > rc) rc = rr;
+  if (A.mixed) {
+    // Mixed layout: the candidates are tested in single precision on the
+    // high words of the positions, against the cutoff widened by a margin
+    // above the single-precision error of the test (a few ulps of the box
+    // edge), so the list holds every pair the exact test would list and a
+    // thin shell more; the pair kernel decides the interaction ranges
+    // exactly.  This keeps the list build off the FP64 pipe.
+    const float4 P = reinterpret_cast<const float4*>(A.pos[nxt])[2 * p];
+    const float Lf[3] = {(float)R.L[0], (float)R.L[1], (float)R.L[2]};
+    const float iLf[3] = {(float)R.iL[0], (float)R.iL[1], (float)R.iL[2]};
+    const float tiltf = (float)R.tilt;
+    const float margin = 1e-6f * fmaxf(Lf[0], fmaxf(Lf[1], Lf[2]));
+    const float fac = (float)rc_fac, rfac = s.rep_on ? (float)s.rep_fac : 0.0f;
+    const float shell = s.structural ? (float)s.shell : 0.0f, skin = (float)s.skin;
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int zz = (cz + dz + ncz) % ncz;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int yy = (cy + dy + ncy) % ncy;
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int xx = (cx + dx + ncx) % ncx;
+          const int64_t key = R.cell_base + ((int64_t)zz * ncy + yy) * ncx + xx;
+          const int q0 = A.cell_start[key], q1 = A.cell_start[key + 1];
+          for (int q = q0; q < q1; ++q) {
+            if (q <= p) continue;
+            const float4 Q = reinterpret_cast<const float4*>(A.pos[nxt])[2 * q];
+            float ry = Q.y - P.y, rx = Q.x - P.x, rz = Q.z - P.z;
+            const float sy = rintf(ry * iLf[1]);
+            ry -= sy * Lf[1];
+            rx -= sy * tiltf;
+            rx -= rintf(rx * iLf[0]) * Lf[0];
+            rz -= rintf(rz * iLf[2]) * Lf[2];
+            const float S = P.w + Q.w;
+            const float rc = fmaxf(fmaxf(S * fac, S * rfac), S + shell * fmaxf(P.w, Q.w)) +
+                             skin + margin + 1e-5f * S;
+            if (!(rx * rx + ry * ry + rz * rz < rc * rc)) continue;
+            if (cnt < kmax) row[(int64_t)cnt * Np] = q;
+            ++cnt;
           }
-          if (s.structural) {
-            const double rs = (P.w + Q.w) + s.shell * (P.w > Q.w ? P.w : Q.w);
-            if (rs > rc) rc = rs;
+        }
+      }
+    }
+  } else {
+    const double L[3] = {R.L[0], R.L[1], R.L[2]};
+    const double iL[3] = {R.iL[0], R.iL[1], R.iL[2]};
+    const double tilt = R.tilt;
+    const double4_32a P = A.pos[nxt][p];
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int zz = (cz + dz + ncz) % ncz;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int yy = (cy + dy + ncy) % ncy;
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int xx = (cx + dx + ncx) % ncx;
+          const int64_t key = R.cell_base + ((int64_t)zz * ncy + yy) * ncx + xx;
+          const int q0 = A.cell_start[key], q1 = A.cell_start[key + 1];
+          for (int q = q0; q < q1; ++q) {
+            if (q <= p) continue;
+            const double4_32a Q = A.pos[nxt][q];
+            double rr[3], sy;
+            min_image_f64(Q.x - P.x, Q.y - P.y, Q.z - P.z, L, iL, tilt, rr, &sy);
+            const double d2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
+            // widest interaction range of the pair (lubrication cutoff,
+            // repulsion range, structural shell), then the skin
+            double rc = (P.w + Q.w) * rc_fac;
+            if (s.rep_on) {
+              const double rq = (P.w + Q.w) * s.rep_fac;
+              if (rq > rc) rc = rq;
+            }
+            if (s.structural) {
+              const double rs = (P.w + Q.w) + s.shell * (P.w > Q.w ? P.w : Q.w);
+              if (rs > rc) rc = rs;
+            }
+            rc = rc + s.skin;
+            if (!(d2 < rc * rc)) continue;
+            if (cnt < kmax) row[(int64_t)cnt * Np] = q;
+            ++cnt;
           }
-          rc = rc + s.skin;
-          if (!(d2 < rc * rc)) continue;
-          if (cnt < kmax) row[(int64_t)cnt * Np] = q;
-          ++cnt;
         }
       }
     }
@@ -297,7 +341,7 @@ __global__ void __launch_bounds__(kBlock) k_remap_history(Arrays A) {
     const int q = A.nbr[nxt][(int64_t)sl * Np + p];
     const double4_32a Q = read_rec_d(A.pos[nxt], A.mixed, q);
     double rr[3], sy;
-    min_image_f64(Q.x - P.x, Q.y - P.y, Q.z - P.z, L, R.tilt, rr, &sy);
+    min_image_f64(Q.x - P.x, Q.y - P.y, Q.z - P.z, L, R.iL, R.tilt, rr, &sy);
     const double d2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
     const double S = P.w + Q.w;
     if (!(sqrt(d2) < S)) continue;  // not touching: history is erased anyway

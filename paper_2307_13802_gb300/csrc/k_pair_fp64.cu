@@ -42,6 +42,7 @@ k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
   const long long k = ctl->k;
   const Replica& RP = A.repl[r];
   const double L[3] = {RP.L[0], RP.L[1], RP.L[2]};
+  const double iL[3] = {RP.iL[0], RP.iL[1], RP.iL[2]};
   const double tilt = RP.tilt;
   const double rate = RP.rate;
   const double eta = RP.eta, kn = RP.kn, kt = RP.kt, mu = RP.mu;
@@ -91,7 +92,7 @@ k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
       const int q = row[(int64_t)sl * Np];
       const double4_32a Q = A.pos[cur][q];
       double rpq[3], sy;
-      min_image_f64(Q.x - P.x, Q.y - P.y, Q.z - P.z, L, tilt, rpq, &sy);
+      min_image_f64(Q.x - P.x, Q.y - P.y, Q.z - P.z, L, iL, tilt, rpq, &sy);
       const double d2 = rpq[0] * rpq[0] + rpq[1] * rpq[1] + rpq[2] * rpq[2];
       const double d = sqrt(d2);
       const double S = ap + Q.w;

@@ -68,7 +68,8 @@ k_pair_stress_noalloc(NoallocArgs a, double* scratch, double* out) {
       const double xi_[3] = {a.x[3 * i], a.x[3 * i + 1], a.x[3 * i + 2]};
       const double xj_[3] = {a.x[3 * j], a.x[3 * j + 1], a.x[3 * j + 2]};
       double r[3], sy;
-      min_image_f64(xj_[0] - xi_[0], xj_[1] - xi_[1], xj_[2] - xi_[2], a.L, a.tilt, r, &sy);
+      const double iL[3] = {1.0 / a.L[0], 1.0 / a.L[1], 1.0 / a.L[2]};
+      min_image_f64(xj_[0] - xi_[0], xj_[1] - xi_[1], xj_[2] - xi_[2], a.L, iL, a.tilt, r, &sy);
       const double d = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
       const double ai = a.radii[i], aj = a.radii[j];
       const double S = ai + aj;

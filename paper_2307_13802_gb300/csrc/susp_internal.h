@@ -48,6 +48,7 @@ constexpr int kErrWrap = 8;
 
 struct Replica {
   double L[3];
+  double iL[3];      // 1 / L
   double rate;       // shear rate
   double rate_dt;    // rate * dt (set per step call)
   double kT;

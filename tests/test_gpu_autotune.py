@@ -1,0 +1,81 @@
+"""The skin setter and the autotuner: changing the skin lays the cell grid
+out again and keeps the physics (forces at a state do not depend on the
+skin), and tuning times the candidates from the current state and puts the
+state back, so a tuned run continues exactly as an untuned one would."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _args(w, precision="fp64"):
+    p = w.params
+    return dict(precision=precision, eta=p["eta"], rho=p["rho"], kn=p["kn"], kt=p["kt"],
+                mu=p["mu"], xi_min=p["xi_min"], xi_max=p["xi_max"], skin=p["skin"],
+                shear_rate=p["shear_rate"], kT=p["kT"], seed=p["seed"],
+                torque_sign=p["torque_sign"], dt=p["dt"])
+
+
+def _relerr(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_skin_changes_neither_forces_nor_trajectory(precision):
+    import paper_2307_13802_gb300 as susp
+
+    w = workloads.make(1200, 0.55, 100.0, 1.0, pack_seed=61, dyn_seed=62)
+    p = w.params
+    out = []
+    for skin in (0.3, 0.05, 0.8):
+        g = susp.System(w.radii, w.box, **_args(w, precision))
+        g.set_state(w.x, w.U, w.W)
+        g.set_skin(skin)
+        g.step(1000, p["shear_rate"], p["kT"], p["dt"], p["seed"])
+        out.append((g.forces()[0], g.info()))
+    F0 = out[0][0]
+    tol = 1e-9 if precision == "fp64" else 1e-3
+    for F, info in out[1:]:
+        assert _relerr(F, F0) <= tol
+    # a smaller skin rebuilds more often and lists fewer pairs
+    assert out[1][1]["nbuilds"] > out[2][1]["nbuilds"]
+    assert out[1][1]["npairs"] < out[2][1]["npairs"]
+
+
+def test_skin_too_large_for_the_box_is_rejected():
+    import paper_2307_13802_gb300 as susp
+
+    w = workloads.make(300, 0.45, 10.0, 0.0, pack_seed=63)
+    g = susp.System(w.radii, w.box, **_args(w))
+    g.set_state(w.x, w.U, w.W)
+    with pytest.raises(susp.SuspError, match="fewer than 3 cells"):
+        g.set_skin(w.L)
+    g.step(5, 1.0, w.params["kT"], 1e-4, 1)   # still usable with the old skin
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotune_restores_the_state(precision):
+    import paper_2307_13802_gb300 as susp
+
+    w = workloads.make(3000, 0.56, 100.0, 1.0, pack_seed=65, dyn_seed=66)
+    p = w.params
+    a = susp.System(w.radii, w.box, **_args(w, precision))
+    b = susp.System(w.radii, w.box, **_args(w, precision))
+    for g in (a, b):
+        g.set_state(w.x, w.U, w.W)
+        g.step(100, p["shear_rate"], p["kT"], p["dt"], p["seed"])
+    chosen, ms = a.autotune(200, p["dt"], [0.15, 0.3, 0.6])
+    assert chosen in (0.15, 0.3, 0.6)
+    assert np.all(np.isfinite(ms)) and np.all(ms > 0)
+    assert ms[[0.15, 0.3, 0.6].index(chosen)] == ms.min()
+    assert a.info()["k"] == b.info()["k"]
+    for g in (a, b):
+        g.step(100, p["shear_rate"], p["kT"], p["dt"], p["seed"])
+    tol = 1e-8 if precision == "fp64" else 1e-3
+    assert _relerr(a.forces()[0], b.forces()[0]) <= tol
+    xa, xb = a.state()[0], b.state()[0]
+    assert np.abs(xa - xb).max() <= (1e-10 if precision == "fp64" else 1e-6)
+    sa, sb = a.stress(), b.stress()
+    assert sa["samples"] == sb["samples"] == 200
