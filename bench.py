@@ -44,9 +44,10 @@ METRIC = "particle-steps/s"
 # with the hash of the source it was taken on; reported only while the
 # source is unchanged.  Filled from profiles/.
 NCU_TRAFFIC = {
-    # ncu --set full, k_pair_mixed<1,1,1,0>, 1M bench workload: 298.3 MB read +
-    # 96.3 MB written per launch (profiles/k_pair_mixed_1M.md)
-    "k_pair_mixed": {"bytes_per_sphere": 394.633, "source_sha": "26bb127685e8aeba"},
+    # ncu --set full on the 1M bench workload (profiles/k_pair_mixed_1M.md,
+    # profiles/k_integrate_mixed_1M.md): DRAM read + write per launch / N
+    "k_pair_mixed": {"bytes_per_sphere": 398.832, "source_sha": "7359f703fe42b905"},
+    "k_integrate_mixed": {"bytes_per_sphere": 272.124, "source_sha": "e9e25bb5f65819be"},
 }
 
 
@@ -167,6 +168,29 @@ def algorithmic_bytes(family: str, precision: str, K: float, c: float, fric: boo
     return 0.0
 
 
+# ---------------------------------------------------------------------------
+# multi-rank pieces (one process per GPU, replicas only)
+# ---------------------------------------------------------------------------
+def rank_seed(seed: int, rank: int) -> int:
+    """Each rank steps an independent replica of the workload: its own
+    dynamics seed, no data exchanged between ranks."""
+    return seed + 7919 * rank
+
+
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's time (the job is done when every rank is)."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, N: int, timesteps: int, ms_max: float) -> float:
+    """Particle-steps per second of the whole job: all ranks' spheres times
+    the timesteps each advanced, over the slowest rank's time."""
+    return world * N * timesteps / (ms_max / 1e3)
+
+
 def run_ours(args, rank, world, local_rank, dist):
     import numpy as np
     import torch
@@ -177,8 +201,7 @@ def run_ours(args, rank, world, local_rank, dist):
     torch.cuda.set_device(local_rank)
     w = workloads.named(WORKLOAD)
     if world > 1:
-        # independent replica per rank: a different dynamics seed
-        w.params["seed"] = w.params["seed"] + 7919 * rank
+        w.params["seed"] = rank_seed(w.params["seed"], rank)
     p = w.params
     N = w.N
     stream = torch.cuda.Stream()
@@ -217,12 +240,10 @@ def run_ours(args, rank, world, local_rank, dist):
     clk = clocks.stop()
     info1 = sysm.info()
     if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, "cuda")
         dist.barrier()
     sig = sysm.stress()
-    value = world * N * args.inner * args.steps / (ms / 1e3)
+    value = job_value(world, N, args.inner * args.steps, ms)
 
     # where the time goes: per-family device time over one more bench step
     prof = sysm.profile(args.inner, p["dt"])

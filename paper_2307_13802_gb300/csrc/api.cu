@@ -52,6 +52,7 @@ struct susp_s {
   int64_t ncell_cap = 0;   // cells the cell arrays hold (the layout of skin 0)
   // block map (host + device)
   std::vector<int> bm_rep, bm_start, bm_end, rep_bstart;
+  std::vector<int> chunk_b, rep_cstart;  // chunks of the stress reduction
   BlockMap bm{};
   // device
   bool allocated = false;
@@ -267,6 +268,13 @@ int common_create(susp_t** out, int32_t R, const int64_t* N_r,
     }
     h->rep_bstart.push_back((int)h->bm_rep.size());
   }
+  // chunks of at most kChunk blocks that never straddle replicas
+  h->rep_cstart.push_back(0);
+  for (int r = 0; r < R; ++r) {
+    for (int b = h->rep_bstart[r]; b < h->rep_bstart[r + 1]; b += kChunk) h->chunk_b.push_back(b);
+    h->rep_cstart.push_back((int)h->chunk_b.size());
+  }
+  h->chunk_b.push_back(h->rep_bstart[R]);
   *out = h;
   return SUSP_OK;
 }
@@ -358,6 +366,10 @@ int allocate(susp_t* h) {
   ok &= alloc_n(h, &A.series, (int64_t)h->R * std::max(A.series_cap, 1));
   ok &= alloc_n(h, &A.series_n, 2 * (int64_t)h->R);
   ok &= alloc_n(h, &A.rep_bstart, h->R + 1);
+  A.nchunk = (int)h->chunk_b.size() - 1;
+  ok &= alloc_n(h, &A.chunk_b, A.nchunk + 1);
+  ok &= alloc_n(h, &A.rep_cstart, h->R + 1);
+  ok &= alloc_n(h, &A.chunk_partial, (int64_t)A.nchunk * (kPartialLen + kKinLen));
   ok &= alloc_n(h, &A.repl, h->R);
   ok &= alloc_n(h, &A.ctl, 1);
   if (h->p0.precision == SUSP_MIXED) {
@@ -383,6 +395,10 @@ int allocate(susp_t* h) {
   CK(cudaMemcpyAsync(bst, h->bm_start.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ben, h->bm_end.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(A.rep_bstart, h->rep_bstart.data(), sizeof(int) * (h->R + 1),
+                     cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(A.chunk_b, h->chunk_b.data(), sizeof(int) * (A.nchunk + 1),
+                     cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(A.rep_cstart, h->rep_cstart.data(), sizeof(int) * (h->R + 1),
                      cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(h->d_radius, h->radii.data(), sizeof(double) * h->N, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(h->d_mass, h->mass.data(), sizeof(double) * h->N, cudaMemcpyHostToDevice, st));
@@ -629,13 +645,14 @@ void enqueue_steps(susp_t* h, int64_t first, int64_t n, double dt,
     }
     launch_pair(h, s, st);
     launch_reduce(h, samp, skin_prev, st);
-    (capture ? h->capture_launches : h->launches) += 2 + ((samp || skin_prev) ? 1 : 0);
+    // integrator + pair kernel, and the two reduction kernels when sampling
+    (capture ? h->capture_launches : h->launches) += 2 + ((samp || skin_prev) ? 2 : 0);
   }
   StepArgs s = make_args(h, dt, 1, 0);
   const int last_kin = sampled(h, first + n - 1);
   launch_finalize(h, s, last_kin, st);
   launch_reduce(h, 0, last_kin, st);
-  (capture ? h->capture_launches : h->launches) += 1 + (last_kin ? 1 : 0);
+  (capture ? h->capture_launches : h->launches) += 1 + (last_kin ? 2 : 0);
 }
 
 int get_graph(susp_t* h, int64_t n, double dt, GraphChunk** out) {

@@ -142,7 +142,6 @@ k_integrate_mixed(Arrays A, BlockMap bm, StepArgs s, int close, int sample_kin,
                   unsigned long long cond_handle, int use_cond, float dt_hi, float dt_lo,
                   float hdt) {
   __shared__ double smem[(kBlock / 32) * kKinLen];
-  __shared__ bool last;
   const int b = blockIdx.x;
   const int r = bm.rep[b];
   const int p = bm.start[b] + threadIdx.x;
@@ -209,15 +208,18 @@ k_integrate_mixed(Arrays A, BlockMap bm, StepArgs s, int close, int sample_kin,
     vpec = sqrtf(vm.x * vm.x + vm.y * vm.y + vm.z * vm.z);
     if (!(vpec == vpec)) vpec = 0.0f;
   }
-  // warp max of the peculiar speed in single precision; non-negative floats
-  // order like their bit patterns, so an integer atomicMax is a float max
+  // Block sums of the kinetic tensors (sampled steps) and the block max of
+  // the peculiar speed in single precision, one barrier for both; thread 0
+  // then publishes the max (non-negative floats order like their bit
+  // patterns, so an integer atomicMax is a float max), fences and takes the
+  // ticket, and the last block runs the step's epilogue.
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ float svmax[kBlock / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) vpec = fmaxf(vpec, __shfl_down_sync(0xffffffffu, vpec, o));
-  if (lane == 0) atomicMax(&ctl->vmax_fbits, __float_as_uint(vpec));
+  if (lane == 0) svmax[warp] = vpec;
+  float* sk = reinterpret_cast<float*>(smem);
   if (close && sample_kin) {
-    // single-precision warp and block sums, double across blocks and time
-    float* sk = reinterpret_cast<float*>(smem);
 #pragma unroll
     for (int q = 0; q < kKinLen; ++q) {
       float v = kin[q];
@@ -225,22 +227,23 @@ k_integrate_mixed(Arrays A, BlockMap bm, StepArgs s, int close, int sample_kin,
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
       if (lane == 0) sk[warp * kKinLen + q] = v;
     }
-    __syncthreads();
-    if (threadIdx.x < kKinLen) {
-      float sum = 0.0f;
-      for (int w2 = 0; w2 < kBlock / 32; ++w2) sum += sk[w2 * kKinLen + threadIdx.x];
-      A.kin_partial[(int64_t)b * kKinLen + threadIdx.x] = (double)sum;
-    }
-  }
-  __threadfence();
-  if (threadIdx.x == 0) {
-    const unsigned int tk = atomicAdd(&ctl->ticket, 1u);
-    last = (tk == (unsigned int)gridDim.x - 1u);
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
+  if (close && sample_kin && threadIdx.x < kKinLen) {
+    float sum = 0.0f;
+    for (int w2 = 0; w2 < kBlock / 32; ++w2) sum += sk[w2 * kKinLen + threadIdx.x];
+    A.kin_partial[(int64_t)b * kKinLen + threadIdx.x] = (double)sum;
+  }
+  if (threadIdx.x == 0) {
+    float bmax = 0.0f;
+    for (int w2 = 0; w2 < kBlock / 32; ++w2) bmax = fmaxf(bmax, svmax[w2]);
+    atomicMax(&ctl->vmax_fbits, __float_as_uint(bmax));
     __threadfence();
-    epilogue_mixed(A, s, cond_handle, use_cond);
+    const unsigned int tk = atomicAdd(&ctl->ticket, 1u);
+    if (tk == (unsigned int)gridDim.x - 1u) {
+      __threadfence();
+      epilogue_mixed(A, s, cond_handle, use_cond);
+    }
   }
 }
 

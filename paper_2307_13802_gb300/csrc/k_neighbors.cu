@@ -333,18 +333,39 @@ __global__ void __launch_bounds__(kBlock) k_remap_history(Arrays A) {
   const int r = A.rep[nxt][p];
   const Replica& R = A.repl[r];
   const double L[3] = {R.L[0], R.L[1], R.L[2]};
-  const double4_32a P = read_rec_d(A.pos[nxt], A.mixed, p);
   const int nn = A.nnb[nxt][p];
   const int op = A.perm[p];
   unsigned long long cm = 0ull;
+  // Only touching pairs keep a history (the next evaluation erases it for
+  // the others), so pairs apart are skipped before the old rows are
+  // searched.  The mixed layout tests in single precision with a margin
+  // above its rounding error: a pair within the margin keeps its history
+  // and the evaluation, which decides contact exactly, erases it if apart.
+  const float4 Pf = reinterpret_cast<const float4*>(A.pos[nxt])[2 * p];
+  const float Lf[3] = {(float)L[0], (float)L[1], (float)L[2]};
+  const float iLf[3] = {(float)R.iL[0], (float)R.iL[1], (float)R.iL[2]};
+  const float tiltf = (float)R.tilt;
+  const float margin = 1e-6f * fmaxf(Lf[0], fmaxf(Lf[1], Lf[2]));
+  const double4_32a P = A.mixed ? double4_32a{} : A.pos[nxt][p];
   for (int sl = 0; sl < nn; ++sl) {
     const int q = A.nbr[nxt][(int64_t)sl * Np + p];
-    const double4_32a Q = read_rec_d(A.pos[nxt], A.mixed, q);
-    double rr[3], sy;
-    min_image_f64(Q.x - P.x, Q.y - P.y, Q.z - P.z, L, R.iL, R.tilt, rr, &sy);
-    const double d2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
-    const double S = P.w + Q.w;
-    if (!(sqrt(d2) < S)) continue;  // not touching: history is erased anyway
+    if (A.mixed) {
+      const float4 Q = reinterpret_cast<const float4*>(A.pos[nxt])[2 * q];
+      float ry = Q.y - Pf.y, rx = Q.x - Pf.x, rz = Q.z - Pf.z;
+      const float sy = rintf(ry * iLf[1]);
+      ry -= sy * Lf[1];
+      rx -= sy * tiltf;
+      rx -= rintf(rx * iLf[0]) * Lf[0];
+      rz -= rintf(rz * iLf[2]) * Lf[2];
+      const float S = (Pf.w + Q.w) * (1.0f + 1e-5f) + margin;
+      if (!(rx * rx + ry * ry + rz * rz < S * S)) continue;
+    } else {
+      const double4_32a Q = A.pos[nxt][q];
+      double rr[3], sy;
+      min_image_f64(Q.x - P.x, Q.y - P.y, Q.z - P.z, L, R.iL, R.tilt, rr, &sy);
+      const double d2 = rr[0] * rr[0] + rr[1] * rr[1] + rr[2] * rr[2];
+      if (!(sqrt(d2) < P.w + Q.w)) continue;
+    }
     const int oq = A.perm[q];
     int row = -1, slot = -1;
     const int n1 = A.nnb[cur][op];

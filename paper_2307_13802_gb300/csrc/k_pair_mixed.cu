@@ -144,7 +144,8 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   __shared__ float4 sT[kBlock];
   __shared__ unsigned long long sM[kBlock];
   __shared__ float sW[(kBlock / 32) * kPartialLen];
-  __shared__ float2 sShx[9];   // x shift dcx w_x + dcy tilt/ncy, double-float
+  __shared__ float2 sShx[9];
+  __shared__ float sA[kBlock];  // radius (high word) of each owner sphere   // x shift dcx w_x + dcy tilt/ncy, double-float
   __shared__ int sArrive;
   const int b = blockIdx.x;
   const int r = bm.rep[b];
@@ -221,6 +222,7 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
       }
     }
     sF[tid] = f;
+    sA[tid] = active ? PM[2 * p].w : 0.0f;
     sT[tid] = t;
     sM[tid] = 0ull;
   }
@@ -246,7 +248,7 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   constexpr int kQ = 64;
   __shared__ int qQ[2][kBlock / 32][kQ];
   __shared__ int qM[2][kBlock / 32][kQ];        // owner lane | slot << 5 | had contact << 12
-  __shared__ float qG[2][kBlock / 32][6][kQ];   // r_x, r_y, r_z, d, h, S
+  __shared__ float qG[2][kBlock / 32][6][kQ];   // r_x, r_y, r_z, h, S, partner radius
   int qn0 = 0, qn1 = 0;
 
   // Pair e of queue qi (1: touching pairs): partner's share by vector
@@ -258,10 +260,11 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
     const int meta = qM[qi][warp][e];
     const int o = meta & 31, sl = (meta >> 5) & 127;
     const float rpq[3] = {qG[qi][warp][0][e], qG[qi][warp][1][e], qG[qi][warp][2][e]};
-    const float d = qG[qi][warp][3][e], h = qG[qi][warp][4][e], S = qG[qi][warp][5][e];
+    const float h = qG[qi][warp][3][e], S = qG[qi][warp][4][e], aq = qG[qi][warp][5][e];
+    const float d = S + h;
     const float xi = 2.0f * h / S;
     const int po = pb + warp * 32 + o;
-    const float4 P = __ldg(PM + 2 * po), Q = __ldg(PM + 2 * q);
+    const float ap = sA[tid - lane + o];
     const float4 WPo = __ldg(OM + po), WQ = __ldg(OM + q);
     const float4 VPo = __ldg(VM + po), VQ = __ldg(VM + q);
     const int tp = __float_as_int(VPo.w), tq = __float_as_int(VQ.w);
@@ -270,7 +273,7 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
     const float id = 1.0f / d;
     const float rr[3] = {sg * rpq[0], sg * rpq[1], sg * rpq[2]};
     const float n[3] = {rr[0] * id, rr[1] * id, rr[2] * id};
-    const float ai = p_is_i ? P.w : Q.w, aj = p_is_i ? Q.w : P.w;
+    const float ai = p_is_i ? ap : aq, aj = p_is_i ? aq : ap;
     const float4 Vi = p_is_i ? VPo : VQ, Vj = p_is_i ? VQ : VPo;
     const float4 Wi4 = p_is_i ? WPo : WQ, Wj4 = p_is_i ? WQ : WPo;
     const float Wi[3] = {Wi4.x, Wi4.y, Wi4.z}, Wj[3] = {Wj4.x, Wj4.y, Wj4.z};
@@ -425,6 +428,22 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   // holds a full batch, else scan the next 32 list items into the queues,
   // else drain what is left.  Phase A and the pair physics each have a
   // single call site, so the kernel body stays small in instruction cache.
+  // list entry of this lane's item in the next phase-A pass, fetched one
+  // pass ahead so that its latency overlaps the current pass and batches
+  int o_n = 0, sl_n = 0, q_n = 0;
+  auto locate = [&](int b0) {
+    const int t = b0 + lane;
+    int o = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int v = __shfl_sync(kFull, incl, o + step - 1);
+      if (v <= t) o += step;
+    }
+    o_n = o;
+    sl_n = t - __shfl_sync(kFull, excl, o);
+    q_n = t < total ? __ldg(nbr + (int64_t)sl_n * Np + pb + warp * 32 + o) : 0;
+  };
+  if (total > 0) locate(0);
   int base = 0;
   while (true) {
     int qi = -1, first = 0, count = 0;
@@ -434,24 +453,16 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
       qi = 1; first = qn1 - 32; count = 32;
     } else if (base < total) {
       const int t = base + lane;
-      // owner lane: first lane whose inclusive row end exceeds t
-      int o = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        const int v = __shfl_sync(kFull, incl, o + step - 1);
-        if (v <= t) o += step;
-      }
-      const int oexcl = __shfl_sync(kFull, excl, o);
+      const int o = o_n, sl = sl_n, q = q_n;
       const unsigned long long ocm = FRIC ? __shfl_sync(kFull, cm_own, o) : 0ull;
+      if (base + 32 < total) locate(base + 32);
       bool keep = false, touch = false;
       float wst = 0.0f, dst = 1.0f, rst[3] = {0.f, 0.f, 0.f};
-      int q = 0, sl = 0;
       float gq[6];
       if (t < total) {
-        sl = t - oexcl;
         const int po = pb + warp * 32 + o;
-        q = __ldg(nbr + (int64_t)sl * Np + po);
         const float4 P = __ldg(PM + 2 * po), Q = __ldg(PM + 2 * q);
+        const float4 Pl = __ldg(PM + 2 * po + 1), Ql = __ldg(PM + 2 * q + 1);
         int pcx, pcy, pcz, qcx, qcy, qcz;
         unpack_cell(__float_as_int(__ldg(&OM[po].w)), pcx, pcy, pcz);
         unpack_cell(__float_as_int(__ldg(&OM[q].w)), qcx, qcy, qcz);
@@ -469,7 +480,6 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
           // separation in double-float from the cell-relative offsets, then
           // d^2 - S^2 with the cancelling squares summed error-free, and the
           // gap h = (d^2 - S^2) / (d + S)
-          const float4 Pl = __ldg(PM + 2 * po + 1), Ql = __ldg(PM + 2 * q + 1);
           const float2 shx = sShx[(dcx + 1) * 3 + (dcy + 1)];
           const float fy = (float)dcy, fz = (float)dcz;
           float rh[3], rl[3];
@@ -509,7 +519,7 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
             keep = true;
             touch = s.contact && h < 0.0f;
             gq[0] = rh[0]; gq[1] = rh[1]; gq[2] = rh[2];
-            gq[3] = d; gq[4] = h; gq[5] = Sh;
+            gq[3] = h; gq[4] = Sh; gq[5] = Q.w;
           }
         }
       }

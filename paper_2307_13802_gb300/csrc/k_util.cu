@@ -136,58 +136,73 @@ __global__ void k_row_counts(Arrays A, int with_history, long long* __restrict__
   else cnt[p] = A.nnb[cur][p];
 }
 
-// grid (R, kPartialLen + kKinLen): component c of replica r summed over the
-// replica's blocks in a fixed order and added to the running accumulator.
-// With a series buffer, the block of the structural xy component also
-// records this sample's Sigma^B_xy = -kT / (shell V) sum w n_x n_y (Eq. 26).
-__global__ void k_reduce_stress(Arrays A, const int* __restrict__ rep_bstart,
-                                int sample_pair, int sample_kin) {
-  __shared__ double smem[kBlock / 32];
-  const int r = blockIdx.x, c = blockIdx.y;
-  const bool is_pair = c < kPartialLen;
-  if (is_pair && !sample_pair) return;
-  if (!is_pair && !sample_kin) return;
-  const int b0 = rep_bstart[r], b1 = rep_bstart[r + 1];
+// Stress reduction in two fixed-order levels (so the result does not depend
+// on scheduling).  Level 1, one block per chunk of up to kChunk consecutive
+// pair-kernel blocks of one replica: thread (g, c) of the 4 x 64 layout sums
+// component c over rows g, g + 4, ... of the chunk (coalesced rows of block
+// partials), and the four row sums are added in order g = 0..3.
+constexpr int kRedLen = kPartialLen + kKinLen;
+static_assert(kRedLen <= 64, "one thread per component and row group");
+
+__global__ void __launch_bounds__(256) k_reduce_chunks(Arrays A, int sample_pair,
+                                                       int sample_kin) {
+  __shared__ double part[4][64];
+  const int ch = blockIdx.x;
+  const int g = threadIdx.x >> 6, c = threadIdx.x & 63;
+  const int b0 = A.chunk_b[ch], b1 = A.chunk_b[ch + 1];
   double s = 0.0;
-  if (is_pair && A.mixed) {
-    // single-precision block partials of the mixed pair kernel, summed per
-    // thread in double-float (two-sum compensation, 48-bit significand)
-    // without FP64-pipe work, then once in double
-    float hi = 0.0f, lo = 0.0f;
-    for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) {
-      const float v = A.pair_partial_w[(int64_t)b * kPartialLen + c];
-      const float t = __fadd_rn(hi, v);
-      const float bb = __fsub_rn(t, hi);
-      const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(v, bb));
-      hi = t;
-      lo = __fadd_rn(lo, e);
+  if (c < kPartialLen && sample_pair) {
+    if (A.mixed) {
+#pragma unroll 4
+      for (int b = b0 + g; b < b1; b += 4) s += (double)A.pair_partial_w[(int64_t)b * kPartialLen + c];
+    } else {
+#pragma unroll 4
+      for (int b = b0 + g; b < b1; b += 4) s += A.pair_partial[(int64_t)b * kPartialLen + c];
     }
-    s = (double)hi + (double)lo;
-  } else {
-    for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x)
-      s += is_pair ? A.pair_partial[(int64_t)b * kPartialLen + c]
-                   : A.kin_partial[(int64_t)b * kKinLen + (c - kPartialLen)];
+  } else if (c >= kPartialLen && c < kRedLen && sample_kin) {
+#pragma unroll 4
+    for (int b = b0 + g; b < b1; b += 4) s += A.kin_partial[(int64_t)b * kKinLen + (c - kPartialLen)];
   }
-  double v[1] = {s};
-  double out[1];
-  __shared__ double res;
-  block_sum_write<1>(v, smem, out);
-  if (threadIdx.x == 0) res = out[0];
+  part[g][c] = s;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double* acc = A.stress_acc + (int64_t)r * kAccStride;
-    acc[c] += res;
-    if (c == 0) acc[kAccNp] += 1.0;
-    if (c == kPartialLen) acc[kAccNk] += 1.0;
-    if (c == kStrOff + 1 && A.series_cap > 0) {
-      const Replica& R = A.repl[r];
-      long long* cnt = A.series_n + 2 * (int64_t)r;
-      if (cnt[0] < A.series_cap) {
-        A.series[(int64_t)r * A.series_cap + cnt[0]] = -R.kT / A.shell * res / R.V;
-        cnt[0] += 1;
-      } else {
-        cnt[1] += 1;
-      }
+  if (g == 0 && c < kRedLen)
+    A.chunk_partial[(int64_t)ch * kRedLen + c] = ((part[0][c] + part[1][c]) + part[2][c]) + part[3][c];
+}
+
+// Level 2, one block per replica: thread (g, c) of the 4 x 64 layout sums
+// component c over the replica's chunks g, g + 4, ... in order, the four
+// sums are added in order g = 0..3, and the result is added to the running
+// accumulator.  With a series buffer, the structural xy component also
+// records this sample's Sigma^B_xy = -kT / (shell V) sum w n_x n_y (Eq. 26).
+__global__ void __launch_bounds__(256) k_reduce_replicas(Arrays A, int sample_pair,
+                                                         int sample_kin) {
+  __shared__ double part[4][64];
+  const int r = blockIdx.x;
+  const int g = threadIdx.x >> 6, c = threadIdx.x & 63;
+  const bool is_pair = c < kPartialLen;
+  const bool on = c < kRedLen && ((is_pair && sample_pair) || (!is_pair && sample_kin));
+  double s = 0.0;
+  if (on) {
+#pragma unroll 4
+    for (int ch = A.rep_cstart[r] + g; ch < A.rep_cstart[r + 1]; ch += 4)
+      s += A.chunk_partial[(int64_t)ch * kRedLen + c];
+  }
+  part[g][c] = s;
+  __syncthreads();
+  if (g != 0 || !on) return;
+  const double tot = ((part[0][c] + part[1][c]) + part[2][c]) + part[3][c];
+  double* acc = A.stress_acc + (int64_t)r * kAccStride;
+  acc[c] += tot;
+  if (c == 0) acc[kAccNp] += 1.0;
+  if (c == kPartialLen) acc[kAccNk] += 1.0;
+  if (c == kStrOff + 1 && A.series_cap > 0) {
+    const Replica& R = A.repl[r];
+    long long* cnt = A.series_n + 2 * (int64_t)r;
+    if (cnt[0] < A.series_cap) {
+      A.series[(int64_t)r * A.series_cap + cnt[0]] = -R.kT / A.shell * tot / R.V;
+      cnt[0] += 1;
+    } else {
+      cnt[1] += 1;
     }
   }
 }
@@ -196,8 +211,8 @@ void launch_reduce_stress(const Arrays& A, const BlockMap& bm, int sample_pair,
                           int sample_kin, cudaStream_t st) {
   (void)bm;
   if (!sample_pair && !sample_kin) return;
-  dim3 grid(A.R, kPartialLen + kKinLen);
-  k_reduce_stress<<<grid, kBlock, 0, st>>>(A, A.rep_bstart, sample_pair, sample_kin);
+  k_reduce_chunks<<<A.nchunk, 256, 0, st>>>(A, sample_pair, sample_kin);
+  k_reduce_replicas<<<A.R, 256, 0, st>>>(A, sample_pair, sample_kin);
 }
 
 // Green-Kubo autocorrelation (Eq. 33): C[m] = sum_{t < n-m} x[t+m] x[t] / (n-m),

@@ -39,6 +39,7 @@ constexpr int kKinLen = 18;          // translational + rotational kinetic
 constexpr int kAccStride = 72;
 constexpr int kAccNp = 63;           // pair samples
 constexpr int kAccNk = 64;           // kinetic samples
+constexpr int kChunk = 64;           // blocks per chunk of the stress reduction
 
 // error bits of Ctl::err
 constexpr int kErrNonFinite = 1;
@@ -198,6 +199,14 @@ struct Arrays {
   int series_cap;
   double shell;         // structural shell Delta / a_i
   int* rep_bstart;      // [R + 1] first block of each replica
+  // two-level stress reduction: chunks of up to kChunk consecutive blocks of
+  // one replica; chunk c covers blocks [chunk_b[c], chunk_b[c + 1]) -- the
+  // array holds nchunk + 1 entries and chunk ends coincide with replica
+  // ends -- and replica r owns chunks [rep_cstart[r], rep_cstart[r + 1])
+  int* chunk_b;
+  int* rep_cstart;
+  int nchunk;
+  double* chunk_partial; // [nchunk][kPartialLen + kKinLen]
   Replica* repl;        // [R]
   Ctl* ctl;
 };

@@ -1,0 +1,97 @@
+"""Statistical validation runs on the GPU (Sec. III.A-B): thousands of
+replicas in one batch handle reproduce the paper's two single-particle and
+two-particle checks.
+
+* Isolated spheres: the mean-square displacement follows Eq. 31,
+  <x^2> = 2 kT m / gamma^2 (gamma t / m - 1 + exp(-gamma t / m)).
+* Two spheres at rest with lubrication, pair noise and contacts: the pair
+  noise is tied to the position-dependent lubrication resistance (Eq. 19),
+  so the stationary distribution is Boltzmann's and, with no force at a gap,
+  the separations beyond contact are uniformly distributed: the pair
+  distribution g(r), hence the potential of mean force -kT ln g, is flat.
+  (A noise amplitude not tied to the resistance, or a wrong sign in Eq. 24,
+  pulls pairs together or apart near contact and the profile bends.)"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(susp, R, n, L, radii, kw):
+    sizes = np.full(R, n, dtype=np.int64)
+    boxes = np.tile([L, L, L], (R, 1))
+    params = [dict(kw, seed=9000 + r) for r in range(R)]
+    return susp.System.batch(sizes, np.tile(radii, R), boxes, params)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_isolated_sphere_msd_follows_eq31(precision):
+    import paper_2307_13802_gb300 as susp
+
+    R, L, kT, dt = 8000, 8.5, 1.0, 2e-3
+    kw = dict(precision=precision, shear_rate=0.0, kT=kT, dt=dt, lubrication=0, contact=0)
+    b = _batch(susp, R, 1, L, [1.0], kw)
+    m, gam = 4.0 / 3.0 * math.pi, 6.0 * math.pi
+    rng = np.random.default_rng(3)
+    x0 = np.full((R, 3), L / 2)
+    b.set_state(x0, rng.normal(scale=math.sqrt(kT / m), size=(R, 3)), None)
+    prev, unwrapped, done = x0.copy(), x0.copy(), 0
+    for t in (25, 100, 400, 1200):
+        b.step_batch(t - done, dt)
+        done = t
+        x, _, _ = b.state()
+        dx = x - prev
+        dx -= np.rint(dx / L) * L
+        unwrapped += dx
+        prev = x
+        msd = np.mean((unwrapped - x0) ** 2)
+        tt = t * dt
+        ref = 2 * kT * m / gam ** 2 * (gam * tt / m - 1 + math.exp(-gam * tt / m))
+        # 3R Gaussian displacements: sd of the mean ~ sqrt(2 / 3R)
+        assert msd == pytest.approx(ref, rel=4 * math.sqrt(2 / (3 * R)) + 0.005), (t, msd, ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_two_sphere_potential_of_mean_force_is_flat(precision):
+    # Starts from the equilibrium distribution (the second sphere uniform in
+    # the box outside contact) and checks that the dynamics keep it: with a
+    # noise amplitude not tied to the resistance the lubrication shell
+    # h <= 0.05 would heat or cool and its population would drift.
+    import paper_2307_13802_gb300 as susp
+
+    R, L, kT, dt = 8000, 8.5, 10.0, 1e-4
+    kw = dict(precision=precision, shear_rate=0.0, kT=kT, dt=dt, mu=0.0)
+    b = _batch(susp, R, 2, L, [1.0, 1.0], kw)
+    rng = np.random.default_rng(11)
+    x = np.empty((R, 2, 3))
+    x[:, 0] = L / 2
+    for r in range(R):
+        while True:
+            y = rng.uniform(0.0, L, size=3)
+            d = y - L / 2
+            d -= np.rint(d / L) * L
+            if np.linalg.norm(d) > 2.02:
+                break
+        x[r, 1] = y
+    m = 4.0 / 3.0 * math.pi
+    U = rng.normal(scale=math.sqrt(kT / m), size=(R, 2, 3))
+    b.set_state(x.reshape(-1, 3), U.reshape(-1, 3), None)
+    b.step_batch(1000, dt)
+    edges = np.array([2.0, 2.05, 2.2, 2.5, 3.0, 3.6])
+    counts = np.zeros(len(edges) - 1)
+    for _ in range(400):
+        b.step_batch(25, dt)
+        xs = b.state()[0].reshape(R, 2, 3)
+        d = xs[:, 1] - xs[:, 0]
+        d -= np.rint(d / L) * L
+        counts += np.histogram(np.linalg.norm(d, axis=1), bins=edges)[0]
+    g = counts / (4.0 / 3.0 * math.pi * (edges[1:] ** 3 - edges[:-1] ** 3))
+    g /= g[1:].mean()
+    print("bins", edges, "g", np.round(g, 4), "counts", counts.astype(int))
+    # samples 25 steps apart are correlated (near contact most): allow four
+    # standard deviations of a count with a correlation factor of 4
+    sd = np.sqrt(4.0 / counts)
+    assert counts.min() > 5_000
+    assert np.all(np.abs(g - 1.0) <= 4 * sd + 0.005), (g, sd)
