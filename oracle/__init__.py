@@ -84,6 +84,8 @@ def lib():
         L.o_set_state.argtypes = [C.c_void_p, _D, _D, _D]
         L.o_set_strain.argtypes = [C.c_void_p, C.c_double]
         L.o_set_k.argtypes = [C.c_void_p, C.c_int64]
+        L.o_set_tags.argtypes = [C.c_void_p, _U32]
+        L.o_set_tags.restype = C.c_int
         L.o_evaluate.argtypes = [C.c_void_p]
         L.o_evaluate.restype = C.c_int
         L.o_build.argtypes = [C.c_void_p]
@@ -246,6 +248,12 @@ class System:
 
     def set_k(self, k: int):
         lib().o_set_k(self._h, int(k))
+
+    def set_tags(self, tags):
+        """Noise-counter tags (increasing with the index)."""
+        t = np.ascontiguousarray(tags, dtype=np.uint32)
+        if len(t) != self.N or lib().o_set_tags(self._h, t.ctypes.data_as(_U32)):
+            raise ValueError("tags must be N values increasing with the index")
 
     def evaluate(self):
         if lib().o_evaluate(self._h):

@@ -106,6 +106,7 @@ typedef struct {
   double tilt;       /* gamma * Ly */
   int64_t k;         /* evaluation index of the forces held in F, T */
   double *a, *m, *I;
+  uint32_t *tag;     /* noise-counter tag of each sphere (default: its index) */
   double *x, *U, *W, *F, *T;
   /* Verlet list */
   o_entry* list;
@@ -451,7 +452,7 @@ static void evaluate(o_sys* s, int advance) {
       double gr = 8.0 * O_PI * p->eta * a * a * a;
       double Uinf[3] = {rate * (x[1] - yc), 0.0, 0.0};
       double g[6] = {0, 0, 0, 0, 0, 0};
-      if (p->noise) o_gaussians6(p->seed, s->k, (uint32_t)i, (uint32_t)i, g);
+      if (p->noise) o_gaussians6(p->seed, s->k, s->tag[i], s->tag[i], g);
       double ct = c * sqrt(gt), cr = c * sqrt(gr);
       for (int q = 0; q < 3; ++q) {
         s->F[3 * i + q] += gt * (Uinf[q] - U[q]) + (p->noise ? ct * g[q] : 0.0);
@@ -523,7 +524,7 @@ static void evaluate(o_sys* s, int advance) {
       o_lubrication(R, n, dU, Wi, Wj, FL, TLi, TLj);
       if (p->noise) {
         double g[6];
-        o_gaussians6(p->seed, s->k, (uint32_t)i, (uint32_t)j, g);
+        o_gaussians6(p->seed, s->k, s->tag[i], s->tag[j], g);
         double th[3] = {g[0], g[1], g[2]};
         double chi[3] = {g[3], g[4], g[5]};
         o_pair_brownian(R, n, th, chi, c, p->torque_sign, FB, TBi, TBj);
@@ -642,6 +643,8 @@ o_sys* o_create(int32_t N, const double* radii, const double box[3],
   s->W = (double*)calloc(n3, sizeof(double));
   s->F = (double*)calloc(n3, sizeof(double));
   s->T = (double*)calloc(n3, sizeof(double));
+  s->tag = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)N);
+  for (int32_t i = 0; i < N; ++i) s->tag[i] = (uint32_t)i;
   /* m = (4/3) pi rho a^3 (Sec. III.B), I = (2/5) m a^2 (Eq. 2) */
   double cm = 4.0 / 3.0 * O_PI * p->rho;
   for (int32_t i = 0; i < N; ++i) {
@@ -656,7 +659,7 @@ o_sys* o_create(int32_t N, const double* radii, const double box[3],
 void o_destroy(o_sys* s) {
   if (!s) return;
   free(s->a); free(s->m); free(s->I); free(s->x); free(s->U); free(s->W);
-  free(s->F); free(s->T); free(s->list);
+  free(s->F); free(s->T); free(s->list); free(s->tag);
   free(s);
 }
 
@@ -678,6 +681,17 @@ void o_set_strain(o_sys* s, double strain) {
 }
 
 void o_set_k(o_sys* s, int64_t k) { s->k = k; s->forces_valid = 0; }
+
+/* Noise-counter tags (Sec. II.C counters use the spheres' tags): lets a
+ * small system stand for spheres of a larger one.  Pairs are still
+ * oriented by index, so tags must increase with the index. */
+int o_set_tags(o_sys* s, const uint32_t* tags) {
+  for (int32_t i = 1; i < s->N; ++i)
+    if (!(tags[i] > tags[i - 1])) return -1;
+  memcpy(s->tag, tags, sizeof(uint32_t) * (size_t)s->N);
+  s->forces_valid = 0;
+  return 0;
+}
 
 /* Force evaluation at the current state without advancing time. */
 int o_evaluate(o_sys* s) {

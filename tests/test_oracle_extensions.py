@@ -153,3 +153,30 @@ def test_green_kubo_fit_recovers_an_exponential_approach():
     step = (10.0 * M) ** (1.0 / 399)        # grid ratio
     assert e_phi == pytest.approx(3.0, rel=5e-3)
     assert 0.37 / step <= tau <= 0.37 * step
+
+
+def test_a_tagged_cluster_reproduces_the_force_on_its_centre():
+    # the forces on a sphere come from the spheres within the interaction
+    # range only, and the noise from (seed, k, tags): a cluster carrying the
+    # global tags reproduces the full system's force and torque on it
+    w = workloads.make(400, 0.52, 10.0, 0.0, pack_seed=95, dyn_seed=96)
+    full = oracle.System(w.radii, w.box, **w.params)
+    full.set_state(w.x, w.U, w.W)
+    full.set_k(3)
+    full.evaluate()
+    F, T = full.forces()
+    L = w.L
+    for c in (7, 123, 301):
+        d = w.x - w.x[c]
+        d -= np.rint(d / L) * L
+        near = np.linalg.norm(d, axis=1) < (w.radii + w.radii[c]) * 1.025 + 1e-9
+        idx = np.flatnonzero(near)             # sorted, includes c
+        o = oracle.System(w.radii[idx], w.box, **w.params)
+        o.set_tags(idx)
+        o.set_state(w.x[idx], w.U[idx], w.W[idx])
+        o.set_k(3)
+        o.evaluate()
+        Fc, Tc = o.forces()
+        k = int(np.flatnonzero(idx == c)[0])
+        assert np.allclose(Fc[k], F[c], rtol=1e-13, atol=1e-13 * np.abs(F).max())
+        assert np.allclose(Tc[k], T[c], rtol=1e-13, atol=1e-13 * np.abs(T).max())
