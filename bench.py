@@ -46,7 +46,10 @@ METRIC = "particle-steps/s"
 NCU_TRAFFIC = {
     # ncu --set full on the 1M bench workload (profiles/k_pair_mixed_1M.md,
     # profiles/k_integrate_mixed_1M.md): DRAM read + write per launch / N
-    "k_pair_mixed": {"bytes_per_sphere": 398.832, "source_sha": "7359f703fe42b905"},
+    # issue_active: fraction of cycles the kernel issued an instruction (the
+    # pair kernel is bound by issue and latency, not by DRAM)
+    "k_pair_mixed": {"bytes_per_sphere": 398.832, "source_sha": "7359f703fe42b905",
+                     "issue_active": 0.696, "dram_throughput": 0.234},
     "k_integrate_mixed": {"bytes_per_sphere": 272.124, "source_sha": "e9e25bb5f65819be"},
 }
 
@@ -268,8 +271,10 @@ def run_ours(args, rank, world, local_rank, dist):
                                                        "k_integrate_fp64.cu")
         rec = NCU_TRAFFIC.get(kernel)
         traffic = None
+        ncu = None
         if rec and rec.get("source_sha") == _src_hash(src):
             traffic = rec["bytes_per_sphere"] * N
+            ncu = {k: rec[k] for k in ("issue_active", "dram_throughput") if k in rec}
         roofline = {"bound": "hbm", "kernel": kernel, "achieved": round(achieved, 1),
                     "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
                     "frac": round(achieved / hbm, 4), "traffic": traffic,
@@ -278,6 +283,8 @@ def run_ours(args, rank, world, local_rank, dist):
                     "ms_per_launch": prof[fam]["ms_per_launch"],
                     "half_list_slots_per_sphere": round(K, 3),
                     "contacts_per_sphere": round(c, 3)}
+        if ncu:
+            roofline["ncu"] = ncu
     breakdown = {f: {"ms_per_launch": round(v["ms_per_launch"], 5),
                      "launches": v["launches"], "ms": round(v["ms"], 3)}
                  for f, v in prof.items()}
