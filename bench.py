@@ -42,10 +42,9 @@ METRIC = "particle-steps/s"
 # DRAM traffic per launch of the dominant kernel from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), recorded per sphere together
 # with the hash of the source it was taken on; reported only while the
-# source is unchanged.  Filled from profiles/.
+# source is unchanged.
 NCU_TRAFFIC = {
-    # ncu --set full on the 1M bench workload (profiles/k_pair_mixed_1M.md,
-    # profiles/k_integrate_mixed_1M.md): DRAM read + write per launch / N
+    # ncu --set full on the 1M bench workload: DRAM read + write per launch / N
     # issue_active: fraction of cycles the kernel issued an instruction (the
     # pair kernel is bound by issue and latency, not by DRAM)
     "k_pair_mixed": {"bytes_per_sphere": 398.832, "source_sha": "7359f703fe42b905",
