@@ -420,7 +420,8 @@ def run_single(susp, w, precision, stream, inner, steps, warmup=1):
 def run_batched(susp, stream, inner=100, steps=3):
     """particle-steps/s of the 256-replica ensemble (N ~ U[500, 20000],
     phi ~ U[0.45, 0.60], Pe log-uniform in [0.1, 1000], mu in {0, 0.5, 1})
-    stepped by one batch handle, mixed precision."""
+    stepped by one batch handle, mixed precision, with the skin picked by the
+    library's autotuner before the timed steps."""
     import numpy as np
     import workloads
     table = workloads.replica_table()
@@ -441,6 +442,10 @@ def run_batched(susp, stream, inner=100, steps=3):
                 np.concatenate([w.W for w in ws]))
     dt = ws[0].params["dt"]
     b.step_batch(inner, dt)
+    # the skin (and with it the cell size) is the autotuner's pick for this
+    # ensemble: timed trials from the current state, which it restores
+    skins = [0.2, 0.3, 0.45, 0.6, 0.8]
+    skin, trial_ms = b.autotune(200, dt, skins)
 
     def run():
         for _ in range(steps):
@@ -453,6 +458,9 @@ def run_batched(susp, stream, inner=100, steps=3):
             "particles": total, "precision": "mixed", "timesteps": inner * steps,
             "ms_per_timestep": round(ms / (inner * steps), 4),
             "finite_eta_r": bool(all(math.isfinite(e) for e in etas)),
+            "skin": skin,
+            "autotune_ms_per_step": {str(k): (round(float(v), 4) if math.isfinite(v) else None)
+                                     for k, v in zip(skins, trial_ms)},
             "packing_tol": 1e-2, "generation_s": round(gen_s, 1)}
 
 
