@@ -47,8 +47,8 @@ NCU_TRAFFIC = {
     # ncu --set full on the 1M bench workload: DRAM read + write per launch / N
     # issue_active: fraction of cycles the kernel issued an instruction (the
     # pair kernel is bound by issue and latency, not by DRAM)
-    "k_pair_mixed": {"bytes_per_sphere": 398.832, "source_sha": "7359f703fe42b905",
-                     "issue_active": 0.696, "dram_throughput": 0.234},
+    "k_pair_mixed": {"bytes_per_sphere": 319.948, "source_sha": "8815575f6cbb6ce9",
+                     "issue_active": 0.693, "dram_throughput": 0.189},
     "k_integrate_mixed": {"bytes_per_sphere": 272.124, "source_sha": "e9e25bb5f65819be"},
 }
 

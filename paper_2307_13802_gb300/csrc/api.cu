@@ -345,7 +345,8 @@ int allocate(susp_t* h) {
     ok &= alloc_n(h, &A.nbr.a[c], (int64_t)h->kmax * Np);
     ok &= alloc_n(h, &A.nnb.a[c], Np);
     ok &= alloc_n(h, &A.cmsk.a[c], Np);
-    if (fric) ok &= alloc_n(h, &A.hist.a[c], 3 * (int64_t)h->kmax * Np);
+    // FP64: [3][kmax][Npad] doubles; mixed: one 32-byte record per slot
+    if (fric) ok &= alloc_n(h, &A.hist.a[c], (A.mixed ? 4 : 3) * (int64_t)h->kmax * Np);
   }
   ok &= alloc_n(h, &A.slot_of_tag, Np);
   ok &= alloc_n(h, &A.cell, Np);
@@ -1004,12 +1005,27 @@ int restore_snapshot(susp_t* h, const Snapshot& sn, const std::string& what) {
       }
     }
     const int64_t hs = (int64_t)h->kmax * Np;
+    std::vector<float> rec(mixed ? (size_t)8 * N : 0);
     for (int sl = 0; sl < m; ++sl) {
       CK(cudaMemcpy(h->A.nbr[cur] + sl * Np, nbr.data() + (size_t)sl * N, sizeof(int) * N,
                     cudaMemcpyHostToDevice));
-      for (int q = 0; q < 3; ++q)
-        CK(cudaMemcpy(h->A.hist[cur] + q * hs + sl * Np, hv.data() + ((size_t)q * m + sl) * N,
-                      sizeof(double) * N, cudaMemcpyHostToDevice));
+      if (mixed) {
+        // 32-byte record per slot: (x_hi, x_lo, y_hi, y_lo), (z_hi, z_lo, 0, 0)
+        for (int64_t i = 0; i < N; ++i)
+          for (int q = 0; q < 3; ++q) {
+            float2 f2;
+            std::memcpy(&f2, &hv[((size_t)q * m + sl) * N + i], sizeof f2);
+            rec[8 * i + 2 * q] = f2.x;
+            rec[8 * i + 2 * q + 1] = f2.y;
+          }
+        for (int64_t i = 0; i < N; ++i) rec[8 * i + 6] = rec[8 * i + 7] = 0.0f;
+        CK(cudaMemcpy(h->A.hist[cur] + 4 * (sl * Np), rec.data(), sizeof(float) * 8 * N,
+                      cudaMemcpyHostToDevice));
+      } else {
+        for (int q = 0; q < 3; ++q)
+          CK(cudaMemcpy(h->A.hist[cur] + q * hs + sl * Np, hv.data() + ((size_t)q * m + sl) * N,
+                        sizeof(double) * N, cudaMemcpyHostToDevice));
+      }
     }
     CK(cudaMemcpy(h->A.nnb[cur], rowlen.data(), sizeof(int) * N, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(h->A.cmsk[cur], cm.data(), sizeof(unsigned long long) * N,

@@ -380,11 +380,19 @@ __global__ void __launch_bounds__(kBlock) k_remap_history(Arrays A) {
     if (!((A.cmsk[cur][row] >> slot) & 1ull)) continue;
     const int64_t src = (int64_t)slot * Np + row;
     const int64_t dst = (int64_t)sl * Np + p;
-    const double* ho = A.hist[cur];
-    double* hn = A.hist[nxt];
-    hn[dst] = ho[src];
-    hn[dst + hs] = ho[src + hs];
-    hn[dst + 2 * hs] = ho[src + 2 * hs];
+    if (A.mixed) {
+      // one 32-byte record per slot
+      const float4* ho = reinterpret_cast<const float4*>(A.hist[cur]);
+      float4* hn = reinterpret_cast<float4*>(A.hist[nxt]);
+      hn[2 * dst] = ho[2 * src];
+      hn[2 * dst + 1] = ho[2 * src + 1];
+    } else {
+      const double* ho = A.hist[cur];
+      double* hn = A.hist[nxt];
+      hn[dst] = ho[src];
+      hn[dst + hs] = ho[src + hs];
+      hn[dst + 2 * hs] = ho[src + 2 * hs];
+    }
     cm |= 1ull << sl;
   }
   A.cmsk[nxt][p] = cm;

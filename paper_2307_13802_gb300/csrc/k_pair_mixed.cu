@@ -16,9 +16,10 @@
 //     accumulators (one vector reduction per sphere at the end), the
 //     partner's share straight to its float4 accumulator with one
 //     red.global.add.v4.f32 for the force and one for the torque.
-//   - Tangential history: double-float (hi, lo) per component, updated with
-//     error-free FP32 transformations (dfloat.cuh), so it accumulates with a
-//     48-bit significand.
+//   - Tangential history: double-float (hi, lo) per component in one
+//     32-byte record per list slot (a touching pair reads and writes one
+//     sector), updated with error-free FP32 transformations (dfloat.cuh), so
+//     it accumulates with a 48-bit significand.
 //   - Stresses: per-lane single-precision virials, warp sums in single
 //     precision, block, global and time sums in double.
 #include <cuda_runtime.h>
@@ -144,8 +145,8 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   __shared__ float4 sT[kBlock];
   __shared__ unsigned long long sM[kBlock];
   __shared__ float sW[(kBlock / 32) * kPartialLen];
-  __shared__ float2 sShx[9];
-  __shared__ float sA[kBlock];  // radius (high word) of each owner sphere   // x shift dcx w_x + dcy tilt/ncy, double-float
+  __shared__ float2 sShx[9];    // x shift dcx w_x + dcy tilt/ncy, double-float
+  __shared__ float sA[kBlock];  // radius (high word) of each owner sphere
   __shared__ int sArrive;
   const int b = blockIdx.x;
   const int r = bm.rep[b];
@@ -175,7 +176,6 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   const uint32_t key0 = RP.key0, key1 = RP.key1;
   const int t0 = (int)RP.p0;
   const int64_t Np = A.Npad;
-  const int64_t hs = (int64_t)A.kmax * Np;
   const float xi_min = s.xi_min_f, xi_max = s.xi_max_f;
   // optional terms: repulsion (Eq. 34) of this replica, structural sums
   // (Eq. 26) on sampled steps; rcf and shf widen the single-precision range
@@ -194,7 +194,9 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   const float4* __restrict__ VM = A.velm;
   const float4* __restrict__ OM = A.omgm;
   const int* __restrict__ nbr = A.nbr[cur];
-  float2* __restrict__ hist = reinterpret_cast<float2*>(A.hist[cur]);
+  // tangential history: one 32-byte record per list slot,
+  // (x_hi, x_lo, y_hi, y_lo), (z_hi, z_lo, -, -)
+  float4* __restrict__ hist = reinterpret_cast<float4*>(A.hist[cur]);
 
   // ---- own sphere: one-body drag and noise (Eqs. 5-6, 20-21) -------------
   int nn = 0;
@@ -317,11 +319,9 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
         float xh[3] = {0.f, 0.f, 0.f}, xl[3] = {0.f, 0.f, 0.f};
         const int64_t hi = (int64_t)sl * Np + po;
         if ((meta >> 12) & 1) {
-#pragma unroll
-          for (int q3 = 0; q3 < 3; ++q3) {
-            const float2 w = hist[hi + q3 * hs];
-            xh[q3] = w.x; xl[q3] = w.y;
-          }
+          const float4 r0 = hist[2 * hi], r1 = hist[2 * hi + 1];
+          xh[0] = r0.x; xl[0] = r0.y; xh[1] = r0.z; xl[1] = r0.w;
+          xh[2] = r1.x; xl[2] = r1.y;
         }
         if (s.advance) {
           const float ww[3] = {ai * Wi[0] + aj * Wj[0], ai * Wi[1] + aj * Wj[1],
@@ -331,8 +331,8 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
           const float vt[3] = {dU[0] - wxn[0], dU[1] - wxn[1], dU[2] - wxn[2]};
           history_update_df(xh, xl, n, vt, dtf, kt, mu * kn * delta);
         }
-#pragma unroll
-        for (int q3 = 0; q3 < 3; ++q3) hist[hi + q3 * hs] = make_float2(xh[q3], xl[q3]);
+        hist[2 * hi] = make_float4(xh[0], xl[0], xh[1], xl[1]);
+        hist[2 * hi + 1] = make_float4(xh[2], xl[2], 0.f, 0.f);
         mbit = 1ull << sl;
         Ft[0] = kt * xh[0]; Ft[1] = kt * xh[1]; Ft[2] = kt * xh[2];
       }

@@ -117,7 +117,7 @@ __global__ void k_list_pairs(Arrays A, const long long* __restrict__ off,
       const int64_t h = (int64_t)sl * Np + p;
       for (int c = 0; c < 3; ++c) {
         if (A.mixed) {
-          const float2 f = reinterpret_cast<const float2*>(A.hist[cur])[h + c * hs];
+          const float2 f = reinterpret_cast<const float2*>(A.hist[cur])[4 * h + c];
           xi_t[3 * o + c] = (double)f.x + (double)f.y;
         } else {
           xi_t[3 * o + c] = A.hist[cur][h + c * hs];

@@ -16,7 +16,9 @@
 //   rep  int32                            replica of the particle
 //   nbr  int32  [kmax][Npad]              half list, slot-major (coalesced)
 //   nnb  int32  [Npad]                    row lengths
-//   hist double [3][kmax][Npad]           tangential history per slot (mu>0)
+//   hist double [3][kmax][Npad]           tangential history per slot (mu>0);
+//                                         mixed: [kmax][Npad] 32-byte records
+//                                         (x, y, z as hi/lo float pairs)
 //   cmsk uint64 [Npad]                    slot s in contact at last evaluation
 //   mirror (mixed precision)  posm: two float4 (hi, lo) of (dx, dy, dz, a),
 //                               the offset from the home-cell origin;
