@@ -359,7 +359,7 @@ int allocate(susp_t* h) {
   ok &= alloc_n(h, &A.scan_part, nparts + 1);
   const int nb = (int)h->bm_rep.size();
   ok &= alloc_n(h, &A.pair_partial, (int64_t)nb * kPartialLen);
-  ok &= alloc_n(h, &A.pair_partial_w, (int64_t)nb * kPartialLen);
+  ok &= alloc_n(h, &A.pair_partial_w, 2 * (int64_t)nb * kPartialLen);
   ok &= alloc_n(h, &A.kin_partial, (int64_t)nb * kKinLen);
   ok &= alloc_n(h, &A.stress_acc, (int64_t)h->R * kAccStride);
   A.series_cap = h->p0.structural ? h->p0.series_cap : 0;
@@ -371,6 +371,8 @@ int allocate(susp_t* h) {
   ok &= alloc_n(h, &A.chunk_b, A.nchunk + 1);
   ok &= alloc_n(h, &A.rep_cstart, h->R + 1);
   ok &= alloc_n(h, &A.chunk_partial, (int64_t)A.nchunk * (kPartialLen + kKinLen));
+  ok &= alloc_n(h, &A.chunk_rep, A.nchunk);
+  ok &= alloc_n(h, &A.rep_tk, h->R);
   ok &= alloc_n(h, &A.repl, h->R);
   ok &= alloc_n(h, &A.ctl, 1);
   if (h->p0.precision == SUSP_MIXED) {
@@ -400,6 +402,11 @@ int allocate(susp_t* h) {
   CK(cudaMemcpyAsync(A.chunk_b, h->chunk_b.data(), sizeof(int) * (A.nchunk + 1),
                      cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(A.rep_cstart, h->rep_cstart.data(), sizeof(int) * (h->R + 1),
+                     cudaMemcpyHostToDevice, st));
+  std::vector<int> chunk_rep(A.nchunk);
+  for (int r = 0; r < h->R; ++r)
+    for (int c = h->rep_cstart[r]; c < h->rep_cstart[r + 1]; ++c) chunk_rep[c] = r;
+  CK(cudaMemcpyAsync(A.chunk_rep, chunk_rep.data(), sizeof(int) * A.nchunk,
                      cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(h->d_radius, h->radii.data(), sizeof(double) * h->N, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(h->d_mass, h->mass.data(), sizeof(double) * h->N, cudaMemcpyHostToDevice, st));
@@ -564,9 +571,10 @@ void launch_finalize(susp_t* h, const StepArgs& s, int sample_kin, cudaStream_t 
   });
 }
 
-void launch_reduce(susp_t* h, int sample_pair, int sample_kin, cudaStream_t st) {
+void launch_reduce(susp_t* h, int sample_pair, int sample_kin, int ppar, cudaStream_t st) {
   if (!sample_pair && !sample_kin) return;
-  timed(h, kFamReduce, st, [&] { launch_reduce_stress(h->A, h->bm, sample_pair, sample_kin, st); });
+  timed(h, kFamReduce, st,
+        [&] { launch_reduce_stress(h->A, h->bm, sample_pair, sample_kin, ppar, st); });
 }
 
 // kernels in one neighbour rebuild (gated sequence of k_neighbors.cu)
@@ -581,7 +589,7 @@ void enqueue_setup_eval(susp_t* h, double dt, int sample, cudaStream_t st) {
   if (h->p0.precision == SUSP_MIXED) launch_mirror(h->A, h->bm, st);
   launch_zero_forces(h->A, st);
   launch_pair(h, s, st);
-  launch_reduce(h, sample, 0, st);
+  launch_reduce(h, sample, 0, s.ppar, st);
 }
 
 bool sampled(const susp_t* h, int64_t step_index) {
@@ -590,15 +598,23 @@ bool sampled(const susp_t* h, int64_t step_index) {
 
 // Enqueue steps [first, first + n) of the run: each step is the fused
 // kick/drift, the (gated) rebuild, the force evaluation and the stress
-// reduction; the chunk ends with the closing half kick.
+// reduction; the chunk ends with the closing half kick.  On the mixed path
+// the reduction of a sampled step runs in the first blocks of the next
+// step's pair kernel, once that step's integrator has summed the kinetic
+// tensors of the same sample (the two pair-partial buffers alternate with
+// the step); the chunk's last sample is reduced after the closing kick.
+// Either way each accumulator receives the samples in step order.
 void enqueue_steps(susp_t* h, int64_t first, int64_t n, double dt,
                    cudaStream_t st, bool capture, std::vector<unsigned long long>* conds) {
+  const bool fused = h->p0.precision == SUSP_MIXED;
   for (int64_t i = 0; i < n; ++i) {
     const int64_t step = first + i;
     const int close = i > 0 ? 1 : 0;
     const int skin_prev = close && sampled(h, step - 1);
     const int samp = sampled(h, step);
     StepArgs s = make_args(h, dt, 1, samp);
+    s.ppar = fused ? (int)(i & 1) : 0;
+    s.fuse_red = fused && skin_prev;
     unsigned long long cond = 0;
     if (capture) {
       cudaStreamCaptureStatus cs;
@@ -645,14 +661,15 @@ void enqueue_steps(susp_t* h, int64_t first, int64_t n, double dt,
       h->launches += rebuild_kernels(h, s);  // gated: launched every step
     }
     launch_pair(h, s, st);
-    launch_reduce(h, samp, skin_prev, st);
+    if (!fused) launch_reduce(h, samp, skin_prev, 0, st);
     // integrator + pair kernel, and the two reduction kernels when sampling
-    (capture ? h->capture_launches : h->launches) += 2 + ((samp || skin_prev) ? 2 : 0);
+    (capture ? h->capture_launches : h->launches) +=
+        2 + ((!fused && (samp || skin_prev)) ? 2 : 0);
   }
   StepArgs s = make_args(h, dt, 1, 0);
   const int last_kin = sampled(h, first + n - 1);
   launch_finalize(h, s, last_kin, st);
-  launch_reduce(h, 0, last_kin, st);
+  launch_reduce(h, fused ? last_kin : 0, last_kin, fused ? (int)((n - 1) & 1) : 0, st);
   (capture ? h->capture_launches : h->launches) += 1 + (last_kin ? 2 : 0);
 }
 

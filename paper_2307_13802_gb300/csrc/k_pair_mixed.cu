@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
+#include "reduce.cuh"
 #include "dfloat.cuh"
 #include "philox.cuh"
 #include "susp_internal.h"
@@ -149,6 +150,12 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   __shared__ float sA[kBlock];  // radius (high word) of each owner sphere
   __shared__ int sArrive;
   const int b = blockIdx.x;
+  // the previous sampled step's stress: block ch < nchunk reduces chunk ch
+  // of it before its own spheres, and the last chunk of a replica sums the
+  // replica (its pair partials are in the other buffer)
+  if (s.fuse_red && b < A.nchunk)
+    reduce_chunk_then_replica(A, b, A.pair_partial_w + (int64_t)(s.ppar ^ 1) * gridDim.x * kPartialLen,
+                              1, 1);
   const int r = bm.rep[b];
   const Replica& RP = A.repl[r];
   if (threadIdx.x == 0) sArrive = 0;
@@ -573,7 +580,8 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
     // single-precision warp sums into shared memory; the last warp of the
     // block to arrive folds the eight warp sums (in warp order) into the
     // block partial, so no warp waits at a block-wide barrier.  Blocks,
-    // replicas and time are summed in double by the reduction kernel.
+    // replicas and time are summed in double by the next pair launch (or the
+    // reduction kernels at the end of a call).
 #pragma unroll
     for (int cc = 0; cc < kVirLen; ++cc) {
       float x = vir[cc];
@@ -595,7 +603,7 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
         float sum = 0.0f;
         for (int w = 0; w < kBlock / 32; ++w)
           sum += *(volatile float*)&sW[w * kPartialLen + src];
-        A.pair_partial_w[(int64_t)b * kPartialLen + cc] = sum;
+        A.pair_partial_w[((int64_t)s.ppar * gridDim.x + b) * kPartialLen + cc] = sum;
       }
     }
   }

@@ -6,6 +6,7 @@
 #include <algorithm>
 
 #include "device_common.cuh"
+#include "reduce.cuh"
 #include "susp_internal.h"
 
 namespace susp {
@@ -136,82 +137,25 @@ __global__ void k_row_counts(Arrays A, int with_history, long long* __restrict__
   else cnt[p] = A.nnb[cur][p];
 }
 
-// Stress reduction in two fixed-order levels (so the result does not depend
-// on scheduling).  Level 1, one block per chunk of up to kChunk consecutive
-// pair-kernel blocks of one replica: thread (g, c) of the 4 x 64 layout sums
-// component c over rows g, g + 4, ... of the chunk (coalesced rows of block
-// partials), and the four row sums are added in order g = 0..3.
-constexpr int kRedLen = kPartialLen + kKinLen;
-static_assert(kRedLen <= 64, "one thread per component and row group");
-
-__global__ void __launch_bounds__(256) k_reduce_chunks(Arrays A, int sample_pair,
-                                                       int sample_kin) {
+// The two levels of the stress reduction as kernels of their own: one block
+// per chunk, then one block per replica (reduce.cuh gives the order).
+__global__ void __launch_bounds__(256) k_reduce_chunks(Arrays A, const float* pw,
+                                                       int sample_pair, int sample_kin) {
   __shared__ double part[4][64];
-  const int ch = blockIdx.x;
-  const int g = threadIdx.x >> 6, c = threadIdx.x & 63;
-  const int b0 = A.chunk_b[ch], b1 = A.chunk_b[ch + 1];
-  double s = 0.0;
-  if (c < kPartialLen && sample_pair) {
-    if (A.mixed) {
-#pragma unroll 4
-      for (int b = b0 + g; b < b1; b += 4) s += (double)A.pair_partial_w[(int64_t)b * kPartialLen + c];
-    } else {
-#pragma unroll 4
-      for (int b = b0 + g; b < b1; b += 4) s += A.pair_partial[(int64_t)b * kPartialLen + c];
-    }
-  } else if (c >= kPartialLen && c < kRedLen && sample_kin) {
-#pragma unroll 4
-    for (int b = b0 + g; b < b1; b += 4) s += A.kin_partial[(int64_t)b * kKinLen + (c - kPartialLen)];
-  }
-  part[g][c] = s;
-  __syncthreads();
-  if (g == 0 && c < kRedLen)
-    A.chunk_partial[(int64_t)ch * kRedLen + c] = ((part[0][c] + part[1][c]) + part[2][c]) + part[3][c];
+  reduce_chunk(A, blockIdx.x, pw, sample_pair, sample_kin, part);
 }
 
-// Level 2, one block per replica: thread (g, c) of the 4 x 64 layout sums
-// component c over the replica's chunks g, g + 4, ... in order, the four
-// sums are added in order g = 0..3, and the result is added to the running
-// accumulator.  With a series buffer, the structural xy component also
-// records this sample's Sigma^B_xy = -kT / (shell V) sum w n_x n_y (Eq. 26).
 __global__ void __launch_bounds__(256) k_reduce_replicas(Arrays A, int sample_pair,
                                                          int sample_kin) {
   __shared__ double part[4][64];
-  const int r = blockIdx.x;
-  const int g = threadIdx.x >> 6, c = threadIdx.x & 63;
-  const bool is_pair = c < kPartialLen;
-  const bool on = c < kRedLen && ((is_pair && sample_pair) || (!is_pair && sample_kin));
-  double s = 0.0;
-  if (on) {
-#pragma unroll 4
-    for (int ch = A.rep_cstart[r] + g; ch < A.rep_cstart[r + 1]; ch += 4)
-      s += A.chunk_partial[(int64_t)ch * kRedLen + c];
-  }
-  part[g][c] = s;
-  __syncthreads();
-  if (g != 0 || !on) return;
-  const double tot = ((part[0][c] + part[1][c]) + part[2][c]) + part[3][c];
-  double* acc = A.stress_acc + (int64_t)r * kAccStride;
-  acc[c] += tot;
-  if (c == 0) acc[kAccNp] += 1.0;
-  if (c == kPartialLen) acc[kAccNk] += 1.0;
-  if (c == kStrOff + 1 && A.series_cap > 0) {
-    const Replica& R = A.repl[r];
-    long long* cnt = A.series_n + 2 * (int64_t)r;
-    if (cnt[0] < A.series_cap) {
-      A.series[(int64_t)r * A.series_cap + cnt[0]] = -R.kT / A.shell * tot / R.V;
-      cnt[0] += 1;
-    } else {
-      cnt[1] += 1;
-    }
-  }
+  reduce_replica(A, blockIdx.x, sample_pair, sample_kin, part);
 }
 
 void launch_reduce_stress(const Arrays& A, const BlockMap& bm, int sample_pair,
-                          int sample_kin, cudaStream_t st) {
-  (void)bm;
+                          int sample_kin, int ppar, cudaStream_t st) {
   if (!sample_pair && !sample_kin) return;
-  k_reduce_chunks<<<A.nchunk, 256, 0, st>>>(A, sample_pair, sample_kin);
+  const float* pw = A.pair_partial_w + (int64_t)ppar * bm.nblocks * kPartialLen;
+  k_reduce_chunks<<<A.nchunk, 256, 0, st>>>(A, pw, sample_pair, sample_kin);
   k_reduce_replicas<<<A.R, 256, 0, st>>>(A, sample_pair, sample_kin);
 }
 

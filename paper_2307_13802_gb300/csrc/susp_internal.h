@@ -193,7 +193,9 @@ struct Arrays {
   int64_t ncell;
   // reductions
   double* pair_partial; // [nblocks][27]
-  float* pair_partial_w; // [nblocks][27] single-precision (mixed path)
+  float* pair_partial_w; // [2][nblocks][45] single-precision (mixed path): two
+                         // buffers, so that a pair launch can reduce the
+                         // previous launch's partials while writing its own
   double* kin_partial;  // [nblocks][18]
   double* stress_acc;   // [R][kAccStride]: 45 pair, 18 kinetic, pair / kinetic counts
   double* series;       // [R][series_cap] Sigma^B_xy per sampled evaluation
@@ -209,6 +211,10 @@ struct Arrays {
   int* rep_cstart;
   int nchunk;
   double* chunk_partial; // [nchunk][kPartialLen + kKinLen]
+  int* chunk_rep;         // [nchunk] replica of each chunk
+  // per-replica arrival counters of the reduction fused into the mixed pair
+  // kernel; zero between launches (the last arrival resets its counter)
+  unsigned int* rep_tk;   // [R]
   Replica* repl;        // [R]
   Ctl* ctl;
 };
@@ -229,6 +235,10 @@ struct StepArgs {
   double shell;      // structural shell Delta / a_i
   int advance;       // 1: time advanced since the previous evaluation
   int sample;        // 1: accumulate stresses at this evaluation
+  int ppar;          // mixed path: pair_partial_w buffer this evaluation writes
+  int fuse_red;      // mixed path: the pair kernel first reduces the previous
+                     // sampled step (buffer ppar ^ 1 and the kinetic partials
+                     // of the integrator launch before it)
   // single-precision copies for the mixed path (set on the host)
   float dt_f, hdt_f, xi_min_f, xi_max_f, tsign_f;
   float rep_fac_f, rep_hc_f, shell_f;
@@ -254,8 +264,9 @@ void launch_pair_mixed(const Arrays& A, const BlockMap& bm, const StepArgs& s,
                        int tpp, cudaStream_t st);
 void launch_autocorr(const double* x, int64_t n, int64_t max_lag, double* C,
                      cudaStream_t st);
+// ppar: the pair_partial_w buffer to read (mixed path)
 void launch_reduce_stress(const Arrays& A, const BlockMap& bm, int sample_pair,
-                          int sample_kin, cudaStream_t st);
+                          int sample_kin, int ppar, cudaStream_t st);
 // neighbour rebuild: `gated` kernels return at once unless ctl->need_rebuild
 void launch_rebuild(const Arrays& A, const BlockMap& bm, const StepArgs& s,
                     cudaStream_t st, int mixed);

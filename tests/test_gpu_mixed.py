@@ -148,3 +148,37 @@ def test_mixed_viscosity_within_one_percent_of_fp64(susp):
     tot32 = res["mixed"]["contact"] + res["mixed"]["lubrication"]
     scale = np.abs(tot64).max()
     assert np.abs(tot32 - tot64).max() <= 1e-2 * scale
+
+
+@pytest.mark.parametrize("sample_every", [1, 3])
+def test_stress_samples_do_not_depend_on_how_steps_are_grouped(susp, sample_every):
+    """The mixed path reduces a sampled step's stress inside the next step's
+    integrator, and a call's last sample after its closing kick.  70 steps as
+    one call (two 32-step graph replays and an eager tail when every step is
+    sampled, all eager when every third one is) and the same steps as 70
+    one-step calls must put the same samples into the accumulators and the
+    series, in the same order.  20,000 spheres make 79 blocks, so a replica
+    spans two reduction chunks.  The two runs differ only by the order of the
+    single-precision force atomics: positions part by ~1e-9 over the 70
+    steps, and the near-contact resistances (1/xi) turn that into ~1e-6
+    relative changes of single pairs.  A lost, repeated or shifted sample
+    moves the averages by percents and the series by its own size."""
+    w = workloads.make(20_000, 0.55, 10.0, 1.0, pack_seed=91, dyn_seed=92)
+    p = w.params
+    res = []
+    for calls in (1, 70):
+        g = _sys(susp, w, "mixed", structural=1, shell=0.05, series_cap=100,
+                 sample_every=sample_every)
+        g.set_state(w.x, w.U, w.W)
+        for _ in range(calls):
+            g.step(70 // calls, p["shear_rate"], p["kT"], p["dt"], p["seed"])
+        res.append((g.state()[0], g.stress(), g.series()))
+    (x1, s1, (q1, d1)), (x2, s2, (q2, d2)) = res
+    n_samples = len(range(0, 70, sample_every))
+    assert s1["samples"] == s2["samples"] == n_samples
+    assert d1 == d2 == 0 and len(q1) == len(q2) == n_samples
+    assert np.abs(q1).max() > 0
+    assert np.abs(q1 - q2).max() <= 1e-6 * np.abs(q1).max()
+    assert np.abs(x1 - x2).max() <= 1e-7
+    for key in ("contact", "lubrication", "brownian", "kinetic", "kinetic_rot", "structural"):
+        assert _relerr(s1[key], s2[key]) <= 1e-5, key
