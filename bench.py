@@ -27,6 +27,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -47,16 +48,27 @@ NCU_TRAFFIC = {
     # ncu --set full on the 1M bench workload: DRAM read + write per launch / N
     # issue_active: fraction of cycles the kernel issued an instruction (the
     # pair kernel is bound by issue and latency, not by DRAM)
-    "k_pair_mixed": {"bytes_per_sphere": 319.948, "source_sha": "8815575f6cbb6ce9",
-                     "issue_active": 0.693, "dram_throughput": 0.189},
+    "k_pair_mixed": {"bytes_per_sphere": 322.416, "source_sha": "268d611af67b21f7",
+                     "issue_active": 0.697, "dram_throughput": 0.189},
     "k_integrate_mixed": {"bytes_per_sphere": 272.124, "source_sha": "e9e25bb5f65819be"},
 }
 
 
 def _src_hash(name: str) -> str:
-    path = os.path.join(ROOT, "paper_2307_13802_gb300", "csrc", name)
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of a kernel's translation unit: the .cu file and every local
+    header it includes, directly or not, in include order."""
+    csrc = os.path.join(ROOT, "paper_2307_13802_gb300", "csrc")
+    h, seen, todo = hashlib.sha256(), set(), [name]
+    while todo:
+        f = todo.pop(0)
+        if f in seen or not os.path.exists(os.path.join(csrc, f)):
+            continue
+        seen.add(f)
+        with open(os.path.join(csrc, f), "rb") as fh:
+            data = fh.read()
+        h.update(data)
+        todo += re.findall(r'^#include "([^"]+)"', data.decode(), flags=re.M)
+    return h.hexdigest()[:16]
 
 
 def parse():
