@@ -152,40 +152,54 @@ k_integrate_mixed(Arrays A, BlockMap bm, StepArgs s, int close, int sample_kin,
   const df tilt{RP.nt_hi, RP.nt_lo};   // tilt after this step's strain advance
   const df ct{RP.nct_hi, RP.nct_lo};
   const df dt{dt_hi, dt_lo};
-  float kin[kKinLen];
-#pragma unroll
-  for (int q = 0; q < kKinLen; ++q) kin[q] = 0.0f;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* sk = reinterpret_cast<float*>(smem);
   float vpec = 0.0f;
+  DF3 x{}, U{}, W{};
+  float a = 0.0f, alo = 0.0f, im = 0.0f, iI = 0.0f;
+  float4 f = make_float4(0.f, 0.f, 0.f, 0.f), t = f;
+  int cellkey = 0, tagp = 0;
+  float4* F4 = reinterpret_cast<float4*>(A.frc[cur]);
+  float4* T4 = reinterpret_cast<float4*>(A.trq[cur]);
   if (active) {
-    DF3 x, U, W;
-    float a, alo, im, iI;
     load_df3(A.pos[cur], p, x, a, &alo);
     load_df3(A.vel[cur], p, U, im);
     load_df3(A.omg[cur], p, W, iI);
-    float4* F4 = reinterpret_cast<float4*>(A.frc[cur]);
-    float4* T4 = reinterpret_cast<float4*>(A.trq[cur]);
-    const float4 f = F4[p], t = T4[p];
-    const int cellkey = A.cell[p];     // issued with the other loads
-    const int tagp = A.tag[cur][p];
-    const float cm = hdt * im, cI = hdt * iI;
-    if (close) {
-      kick(U, f, cm);
-      kick(W, t, cI);
-      if (sample_kin) {
+    f = F4[p];
+    t = T4[p];
+    cellkey = A.cell[p];     // issued with the other loads
+    tagp = A.tag[cur][p];
+  }
+  const float cm = hdt * im, cI = hdt * iI;
+  if (close) {
+    kick(U, f, cm);
+    kick(W, t, cI);
+    if (sample_kin) {
+      // kinetic tensors of the closed step, summed over the warp one entry
+      // at a time into shared memory (all lanes take part; idle lanes add 0)
+      float u[3] = {0.f, 0.f, 0.f}, w[3] = {0.f, 0.f, 0.f}, m = 0.f, I = 0.f;
+      if (active) {
         const df yrel = df_sub(x.y, df{RP.yc_hi, RP.yc_lo});
-        const float u[3] = {df_to_f(df_sub(U.x, df_mul(yrel, df{RP.rate_hi, RP.rate_lo}))),
-                            df_to_f(U.y), df_to_f(U.z)};
-        const float w[3] = {df_to_f(W.x), df_to_f(W.y), df_to_f(W.z) + 0.5f * RP.rate_f};
-        const float m = 1.0f / im, I = 1.0f / iI;
+        u[0] = df_to_f(df_sub(U.x, df_mul(yrel, df{RP.rate_hi, RP.rate_lo})));
+        u[1] = df_to_f(U.y);
+        u[2] = df_to_f(U.z);
+        w[0] = df_to_f(W.x);
+        w[1] = df_to_f(W.y);
+        w[2] = df_to_f(W.z) + 0.5f * RP.rate_f;
+        m = 1.0f / im;
+        I = 1.0f / iI;
+      }
 #pragma unroll
-        for (int al = 0; al < 3; ++al)
+      for (int q = 0; q < kKinLen; ++q) {
+        const int al = (q % 9) / 3, be = q % 3;
+        float v = q < 9 ? m * u[al] * u[be] : I * w[al] * w[be];
 #pragma unroll
-          for (int be = 0; be < 3; ++be) {
-            kin[3 * al + be] = m * u[al] * u[be];
-            kin[9 + 3 * al + be] = I * w[al] * w[be];
-          }
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sk[warp * kKinLen + q] = v;
       }
     }
+  }
+  if (active) {
     kick(U, f, cm);
     kick(W, t, cI);
     x.x = df_add(x.x, df_mul(U.x, dt));
@@ -208,26 +222,16 @@ k_integrate_mixed(Arrays A, BlockMap bm, StepArgs s, int close, int sample_kin,
     vpec = sqrtf(vm.x * vm.x + vm.y * vm.y + vm.z * vm.z);
     if (!(vpec == vpec)) vpec = 0.0f;
   }
-  // Block sums of the kinetic tensors (sampled steps) and the block max of
-  // the peculiar speed in single precision, one barrier for both; thread 0
-  // then publishes the max (non-negative floats order like their bit
-  // patterns, so an integer atomicMax is a float max), fences and takes the
-  // ticket, and the last block runs the step's epilogue.
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // Block sums of the kinetic tensors (sampled steps; the warp sums are in
+  // shared memory already) and the block max of the peculiar speed in single
+  // precision, one barrier for both; thread 0 then publishes the max
+  // (non-negative floats order like their bit patterns, so an integer
+  // atomicMax is a float max), fences and takes the ticket, and the last
+  // block runs the step's epilogue.
   __shared__ float svmax[kBlock / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) vpec = fmaxf(vpec, __shfl_down_sync(0xffffffffu, vpec, o));
   if (lane == 0) svmax[warp] = vpec;
-  float* sk = reinterpret_cast<float*>(smem);
-  if (close && sample_kin) {
-#pragma unroll
-    for (int q = 0; q < kKinLen; ++q) {
-      float v = kin[q];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) sk[warp * kKinLen + q] = v;
-    }
-  }
   __syncthreads();
   if (close && sample_kin && threadIdx.x < kKinLen) {
     float sum = 0.0f;
