@@ -50,7 +50,7 @@ NCU_TRAFFIC = {
     # pair kernel is bound by issue and latency, not by DRAM)
     "k_pair_mixed": {"bytes_per_sphere": 322.416, "source_sha": "268d611af67b21f7",
                      "issue_active": 0.697, "dram_throughput": 0.189},
-    "k_integrate_mixed": {"bytes_per_sphere": 272.124, "source_sha": "e9e25bb5f65819be"},
+    "k_integrate_mixed": {"bytes_per_sphere": 268.032, "source_sha": "a36871f83c3d4e1f"},
 }
 
 
