@@ -20,8 +20,9 @@
 //     32-byte record per list slot (a touching pair reads and writes one
 //     sector), updated with error-free FP32 transformations (dfloat.cuh), so
 //     it accumulates with a 48-bit significand.
-//   - Stresses: per-lane single-precision virials, warp sums in single
-//     precision, block, global and time sums in double.
+//   - Stresses: single-precision virials summed over the warp batch by batch
+//     (a reduce-scatter leaves entry l in lane l), block sums in single
+//     precision, global and time sums in double.
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
@@ -130,10 +131,29 @@ __device__ __forceinline__ int wrap_dc(int d, int n) {
   return d > 1 ? d - n : (d < -1 ? d + n : d);
 }
 
-// resident blocks per SM the register allocation targets (3 measured
-// fastest at N = 1M: 80 registers with a few bytes of spill beat 124 at 2)
+// Sums v[0..31] over the 32 lanes of a warp and leaves the total of
+// component l in lane l: five halving stages, in each of which a lane keeps
+// one half of its components and adds the partner's copy of that half
+// (lane ^ offset).  31 shuffles per lane instead of 5 per component.
+__device__ __forceinline__ float warp_reduce_scatter32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < off; ++i) {
+      const float send = up ? v[i] : v[i + off];
+      const float keep = up ? v[i + off] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  return v[0];
+}
+
+// resident blocks per SM the register allocation targets (4 measured
+// fastest at N = 1M: 64 registers without spills; 3 blocks at 80 registers
+// took 0.214 ms against 0.201 ms)
 #ifndef SUSP_PAIR_MINBLOCKS
-#define SUSP_PAIR_MINBLOCKS 3
+#define SUSP_PAIR_MINBLOCKS 4
 #endif
 
 // EXTRA: the optional repulsion (Eq. 34) and structural sums (Eq. 26) are
@@ -246,9 +266,10 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   const int excl = incl - nn;
   __syncwarp();
 
-  float vir[SAMPLE ? kVirLen : 1];
-#pragma unroll
-  for (int q = 0; q < (SAMPLE ? kVirLen : 1); ++q) vir[q] = 0.0f;
+  // pair virials C, HL, BL (27 entries): each batch's 32 pairs are summed
+  // over the warp as they are formed, and lane l keeps the running warp
+  // total of entry l
+  float vacc = 0.0f;
 
   // Pairs within the cutoff are queued per warp in shared memory, touching
   // pairs (queue 1) apart from the others (queue 0), and the pair physics
@@ -264,7 +285,7 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   // reductions, owner's share returned in v (force, torque) with its contact
   // bit; returns the owner.  qi is warp-uniform.
   auto physics = [&](int qi, int e, float* v, unsigned long long& mbit, float* FR,
-                     float* rro) -> int {
+                     float* rro, float* vp) -> int {
     const int q = qQ[qi][warp][e];
     const int meta = qM[qi][warp][e];
     const int o = meta & 31, sl = (meta >> 5) & 127;
@@ -371,9 +392,9 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
       for (int al = 0; al < 3; ++al)
 #pragma unroll
         for (int be = 0; be < 3; ++be) {
-          vir[3 * al + be] += FC[al] * rr[be];
-          vir[9 + 3 * al + be] += ou.FL[al] * rr[be];
-          vir[18 + 3 * al + be] += ou.FB[al] * rr[be];
+          vp[3 * al + be] = FC[al] * rr[be];
+          vp[9 + 3 * al + be] = ou.FL[al] * rr[be];
+          vp[18 + 3 * al + be] = ou.FB[al] * rr[be];
         }
     }
     return o;
@@ -389,7 +410,11 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
     unsigned long long mb = 0ull;
     int own = 32;  // idle lanes: past every owner
     float FR[3] = {0.f, 0.f, 0.f}, rro[3] = {0.f, 0.f, 0.f};
-    if (lane < count) own = physics(qi, first + lane, v, mb, FR, rro);
+    float vp[32];
+#pragma unroll
+    for (int cc = 0; cc < 32; ++cc) vp[cc] = 0.0f;
+    if (lane < count) own = physics(qi, first + lane, v, mb, FR, rro, vp);
+    if (SAMPLE) vacc += warp_reduce_scatter32(vp, lane);
     if (SAMPLE && rep_on) {
       // repulsion virial F^R (x) r summed over the warp into its slots
 #pragma unroll
@@ -582,13 +607,8 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
     // block partial, so no warp waits at a block-wide barrier.  Blocks,
     // replicas and time are summed in double by the next pair launch (or the
     // reduction kernels at the end of a call).
-#pragma unroll
-    for (int cc = 0; cc < kVirLen; ++cc) {
-      float x = vir[cc];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFull, x, o);
-      if (lane == 0) sW[warp * kPartialLen + cc] = x;
-    }
+    if (lane < kVirLen) sW[warp * kPartialLen + lane] = vacc;
+    __syncwarp();
     __threadfence_block();
     int arrived = 0;
     if (lane == 0) arrived = atomicAdd(&sArrive, 1);
