@@ -48,8 +48,8 @@ NCU_TRAFFIC = {
     # ncu --set full on the 1M bench workload: DRAM read + write per launch / N
     # issue_active: fraction of cycles the kernel issued an instruction (the
     # pair kernel is bound by issue and latency, not by DRAM)
-    "k_pair_mixed": {"bytes_per_sphere": 322.416, "source_sha": "268d611af67b21f7",
-                     "issue_active": 0.697, "dram_throughput": 0.189},
+    "k_pair_mixed": {"bytes_per_sphere": 314.386, "source_sha": "2cdd6539e7f8d9fc",
+                     "issue_active": 0.779, "dram_throughput": 0.200},
     "k_integrate_mixed": {"bytes_per_sphere": 268.032, "source_sha": "a36871f83c3d4e1f"},
 }
 
