@@ -60,6 +60,30 @@ def test_mixed_one_evaluation_without_noise(susp, strain, poly):
         assert _relerr(s32[key], s64[key]) <= RTOL_MIXED, key
 
 
+def test_mixed_brownian_stress_tracks_fp64_with_noise(susp):
+    """One evaluation with the pair noise on.  Both paths draw the same Philox
+    words; the mixed one maps them through 24-bit uniforms and the fast
+    log/sin/cos, so single deviates differ by ~1e-6 relative and rarely (a
+    uniform within 2^-24 of 0) by more.  The Brownian stress is a sum over
+    thousands of pairs and agrees to well within 5e-3 of its largest entry;
+    a wrong entry of the 27 virial slots would be off by its own size."""
+    w = workloads.make(3000, 0.58, 10.0, 1.0, pack_seed=55, dyn_seed=56)
+    w.x = w.x * 0.99
+    w.L = w.L * 0.99
+    res = {}
+    for prec in ("fp64", "mixed"):
+        g = _sys(susp, w, prec)
+        g.set_state(w.x, w.U, w.W)
+        g.set_clock(7, 0.3)
+        g.evaluate()
+        res[prec] = g.stress()
+    s64, s32 = res["fp64"], res["mixed"]
+    assert np.abs(s64["brownian"]).max() > 0
+    for key in ("contact", "lubrication"):
+        assert _relerr(s32[key], s64[key]) <= RTOL_MIXED, key
+    assert _relerr(s32["brownian"], s64["brownian"]) <= 5e-3
+
+
 @pytest.mark.parametrize("start_strain", [0.1, 0.495])
 def test_mixed_trajectory_tracks_fp64_without_noise(susp, start_strain):
     # 400 steps with rebuilds (and, from 0.495, a strain flip)
