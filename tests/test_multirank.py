@@ -40,9 +40,11 @@ def test_two_gloo_ranks_time_the_slowest_and_count_all_spheres():
     procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
     for p in procs:
         p.start()
-    out = sorted(q.get(timeout=120) for _ in procs)
+    # each child imports torch first, which can take minutes on a cold,
+    # loaded machine
+    out = sorted(q.get(timeout=600) for _ in procs)
     for p in procs:
-        p.join(timeout=60)
+        p.join(timeout=120)
         assert p.exitcode == 0
     (r0, s0, m0, v0), (r1, s1, m1, v1) = out
     assert (r0, r1) == (0, 1)
