@@ -1,6 +1,9 @@
 // k_pair_fp64.cu -- per-timestep pair force evaluation in double precision
 // (the plain FP64 path).  Compiled without multiply-add contraction so that
-// every sum and product rounds as written.
+// every sum and product rounds as written; the resistances and the unit
+// vector use reciprocal products in place of the printed quotients (a few
+// ulps from the printed forms), which takes the FP64 divisions, each a long
+// sequence on the FP64 pipe, from 21 to 10 per lubricated pair.
 //
 // One thread per sphere p of the sorted order walks its half-list row.  For
 // each listed pair it forms the minimum-image gap h = |r| - (a_i + a_j) and
@@ -28,6 +31,41 @@
 #include "susp_internal.h"
 
 namespace susp {
+
+// Scalar resistances of Eqs. 9-12 and 15-18 with the quotients of the
+// printed forms taken as products with four reciprocals (beta = a_j/a_i,
+// r = 1/(1 + beta), 1/beta, ixi = 1/xi_e); algebraically the same, and
+// within a few ulps of the printed forms (1/(1 + 1/beta) = beta r):
+//   XA11 = 6 pi eta a_i r^3 (2 beta^2 ixi + beta (1 + 7 beta + beta^2)/5 L)
+//   YA11 = 6 pi eta a_i r^3 (4 beta (2 + beta + 2 beta^2)/15) L
+//   YB11 = -4 pi eta a_i^2 r^2 (beta (4 + beta)/5) L
+//   YB21 = -4 pi eta a_j^2 r^2 ((4 beta + 1)/5) L
+//   YC11 = 8 pi eta a_i^3 r (2 beta/5) L,   YC12 = 8 pi eta a_i^3 r (beta^2/10) L
+//   YC22 = 8 pi eta a_j^3 r (2/5) L,        YC21 = 8 pi eta a_j^3 r (1/(10 beta)) L
+// with L = ln(1/xi_e).
+__device__ __forceinline__ Res8<double> resistances_rcp(double eta, double ai, double aj,
+                                                        double ixi, double L) {
+  const double pi = 3.14159265358979323846;
+  const double beta = aj / ai;
+  const double ibeta = ai / aj;
+  const double r = 1.0 / (1.0 + beta);
+  const double r2 = r * r, r3 = r2 * r;
+  const double b2 = beta * beta;
+  const double ta = 6.0 * pi * eta * ai * r3;
+  Res8<double> R;
+  R.XA11 = ta * (2.0 * b2 * ixi + 0.2 * beta * (1.0 + 7.0 * beta + b2) * L);
+  R.YA11 = ta * ((4.0 / 15.0) * beta * (2.0 + beta + 2.0 * b2) * L);
+  const double tb = -4.0 * pi * eta * r2 * 0.2 * L;
+  R.YB11 = tb * ai * ai * (beta * (4.0 + beta));
+  R.YB21 = tb * aj * aj * (4.0 * beta + 1.0);
+  const double tc = 8.0 * pi * eta * r * L;
+  const double ai3 = ai * ai * ai, aj3 = aj * aj * aj;
+  R.YC11 = tc * ai3 * (0.4 * beta);
+  R.YC12 = tc * ai3 * (0.1 * b2);
+  R.YC22 = tc * aj3 * 0.4;
+  R.YC21 = tc * aj3 * (0.1 * ibeta);
+  return R;
+}
 
 template <bool NOISE, bool FRIC, bool SAMPLE>
 __global__ void __launch_bounds__(kBlock)
@@ -123,7 +161,8 @@ k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
         Ui[0] = VQ.x; Ui[1] = VQ.y; Ui[2] = VQ.z; Uj[0] = VP.x; Uj[1] = VP.y; Uj[2] = VP.z;
         Wi[0] = WQ.x; Wi[1] = WQ.y; Wi[2] = WQ.z; Wj[0] = WP.x; Wj[1] = WP.y; Wj[2] = WP.z;
       }
-      const double n[3] = {rr[0] / d, rr[1] / d, rr[2] / d};
+      const double id = 1.0 / d;
+      const double n[3] = {rr[0] * id, rr[1] * id, rr[2] * id};
       const double dU[3] = {Uj[0] - syij * rate * L[1] - Ui[0], Uj[1] - Ui[1],
                             Uj[2] - Ui[2]};
 
@@ -144,8 +183,9 @@ k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
       PairOut<double> o;
       if (lub && s.lubrication) {
         const double xi_e = xi < s.xi_min ? s.xi_min : xi;
-        const double lg = log(1.0 / xi_e);
-        const Res8<double> R = resistances<double>(eta, ai, aj, xi_e, lg);
+        const double ixi = 1.0 / xi_e;
+        const double lg = log(ixi);
+        const Res8<double> R = resistances_rcp(eta, ai, aj, ixi, lg);
         double g[6] = {0, 0, 0, 0, 0, 0};
         const int li = (int)((p_is_i ? tp : tq) - t0);
         const int lj = (int)((p_is_i ? tq : tp) - t0);

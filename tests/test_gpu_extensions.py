@@ -3,8 +3,9 @@ repulsion (Eq. 34), the structural Brownian stress (Eq. 26) with its
 per-sample series, and the Green-Kubo integral (Eq. 33).
 
 Same bars as the core parity tests: the FP64 path evaluates the oracle's
-expressions (no multiply-add contraction) and differs only in the summation
-order, so one evaluation agrees to 1e-11 of the largest entry and the
+expressions (no multiply-add contraction; reciprocal products in the
+resistances, a few ulps) and otherwise differs only in the summation order,
+so one evaluation agrees to 1e-11 of the largest entry and the
 neighbour sets, decided by the same double expression, agree exactly.  The
 shell counts of Eq. 26 are integer decisions on the same double gap, so the
 structural stress agrees to the same 1e-11.  The mixed path forms gaps and

@@ -1,9 +1,11 @@
 """GPU parity: the CUDA library (through the C ABI) against the FP64 oracle
 on the same seeded inputs.
 
-Tolerances: the FP64 path evaluates the same expressions as the oracle with
-no multiply-add contraction; they differ only in the last bits of log, sin,
-cos (CUDA vs libm) and in the order of the force sums (atomics).  So forces,
+Tolerances: the FP64 path evaluates the oracle's expressions with no
+multiply-add contraction, except that the resistances and the unit vector
+take reciprocal products in place of the printed quotients (a few ulps);
+beyond that they differ only in the last bits of log, sin, cos (CUDA vs libm)
+and in the order of the force sums (atomics).  So forces,
 torques and stresses of one evaluation agree to 1e-11 relative to the
 largest entry of the same quantity (normwise), and neighbour sets, which are
 decided by the same d^2 < r_list^2 expression, agree exactly."""
