@@ -83,6 +83,7 @@ def lib():
         L.o_destroy.argtypes = [C.c_void_p]
         L.o_set_state.argtypes = [C.c_void_p, _D, _D, _D]
         L.o_set_strain.argtypes = [C.c_void_p, C.c_double]
+        L.o_set_velocities.argtypes = [C.c_void_p, _D, _D]
         L.o_set_k.argtypes = [C.c_void_p, C.c_int64]
         L.o_set_tags.argtypes = [C.c_void_p, _U32]
         L.o_set_tags.restype = C.c_int
@@ -242,6 +243,11 @@ class System:
         W = None if W is None else _f64(W, (self.N, 3))
         lib().o_set_state(self._h, _dp(x), _dp(U) if U is not None else None,
                           _dp(W) if W is not None else None)
+
+    def set_velocities(self, U, W):
+        """New velocities; positions, list and tangential history are kept."""
+        U, W = _f64(U, (self.N, 3)), _f64(W, (self.N, 3))
+        lib().o_set_velocities(self._h, _dp(U), _dp(W))
 
     def set_strain(self, strain: float):
         lib().o_set_strain(self._h, float(strain))

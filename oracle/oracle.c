@@ -53,7 +53,14 @@
  * known-answer vectors, the isolated-particle mean-square displacement
  * (Eq. 31), exact discrete equipartition of the Velocity-Verlet/Langevin map,
  * the Einstein limit of the drag stresslet, the Coulomb cap, image and flip
- * invariance, and the Pe definition against Table 1.
+ * invariance, and the Pe definition against Table 1.  The tangential history
+ * and contact torque (Eqs. 3-4) are pinned by closed forms built from the
+ * rigid-body velocities of the two contact points: a history growing as the
+ * tangential slip times t with F = k_t xi and torques a n x F at each contact
+ * point, no history for spheres rolling on each other, a capped force of
+ * magnitude mu k_n delta against the slip, a history that turns with the
+ * contact normal at constant length when nothing slips, and the energy of a
+ * frictional collision conserved as dt -> 0.
  */
 #include <math.h>
 #include <stdint.h>
@@ -671,6 +678,15 @@ void o_set_state(o_sys* s, const double* x, const double* U, const double* W) {
   for (int32_t i = 0; i < s->N; ++i) wrap_particle(s, i);
   s->have_list = 0;
   s->nlist = 0;
+  s->forces_valid = 0;
+}
+
+/* Replaces velocities and angular velocities (N x 3 each) and keeps the
+ * positions, the Verlet list and the tangential history. */
+void o_set_velocities(o_sys* s, const double* U, const double* W) {
+  size_t n3 = 3 * (size_t)s->N;
+  memcpy(s->U, U, sizeof(double) * n3);
+  memcpy(s->W, W, sizeof(double) * n3);
   s->forces_valid = 0;
 }
 

@@ -411,3 +411,246 @@ def test_equipartition_in_a_dense_suspension_at_rest():
                                 mp_context=ctx) as ex:
         temps = list(ex.map(_equipartition_run, range(16)))
     assert np.mean(temps) == pytest.approx(1.0, abs=0.015), temps
+
+
+# --------------------------------------------------------------------------
+# friction: tangential history and contact torque (Sec. II.A, Eqs. 3-4)
+#
+# Two spheres of unequal radii touch along a general direction n.  The
+# velocities of their surface points at the contact follow from rigid-body
+# kinematics, v_c,i = U_i + Omega_i x (a_i n) and v_c,j = U_j + Omega_j x
+# (-a_j n); the stored history is the accumulated tangential part of
+# v_c,j - v_c,i.  With the positions frozen (n fixed) and the spheres made
+# so heavy that the forces do not change their velocities, the history grows
+# exactly linearly, so every quantity has a closed form.  The tangential
+# spring acts on i at i's contact point (lever arm a_i n) and its reaction on
+# j at j's contact point (lever arm -a_j n).
+# --------------------------------------------------------------------------
+_AI, _AJ, _KN, _KT, _DELTA, _DT = 1.0, 1.4, 1e4, 5e3, 0.01, 1e-4
+_N_DIR = np.array([0.3, -0.5, 0.81]) / np.linalg.norm([0.3, -0.5, 0.81])
+
+
+def _frozen_pair(U, W, mu):
+    L = 20.0
+    d = _AI + _AJ - _DELTA
+    x = np.array([[8.0, 9.0, 7.5], [8.0, 9.0, 7.5]])
+    x[1] += d * _N_DIR
+    s = oracle.System([_AI, _AJ], [L, L, L], kn=_KN, kt=_KT, mu=mu, rho=1e30,
+                      shear_rate=0.0, kT=0.0, dt=_DT, noise=0, lubrication=0,
+                      onebody=0, freeze=1)
+    s.set_state(x, U, W)
+    return s, L
+
+
+def _contact_slip(U, W):
+    """Tangential part of the velocity of j's contact point relative to i's."""
+    n = _N_DIR
+    vci = U[0] + np.cross(W[0], _AI * n)
+    vcj = U[1] + np.cross(W[1], -_AJ * n)
+    v = vcj - vci
+    return v - np.dot(v, n) * n
+
+
+@pytest.mark.parametrize("case", ["slide", "spin_i", "spin_j", "general"])
+def test_history_grows_as_the_contact_slip_times_t(case):
+    rng = np.random.default_rng({"slide": 1, "spin_i": 2, "spin_j": 3, "general": 4}[case])
+    U = np.zeros((2, 3))
+    W = np.zeros((2, 3))
+    if case in ("slide", "general"):
+        U = rng.normal(size=(2, 3))
+    if case in ("spin_i", "general"):
+        W[0] = rng.normal(size=3)
+    if case in ("spin_j", "general"):
+        W[1] = rng.normal(size=3)
+    s, L = _frozen_pair(U, W, mu=1e12)
+    nsteps = 37
+    s.step(nsteps)
+    _, hist, contact = s.verlet_list()
+    assert contact[0] == 1
+    xi_ref = _contact_slip(U, W) * (nsteps * _DT)
+    assert np.linalg.norm(xi_ref) > 1e-4
+    assert np.abs(hist[0] - xi_ref).max() <= 1e-12 * np.linalg.norm(xi_ref)
+    # forces: normal spring plus the tangential spring k_t xi on i, the
+    # reaction on j; torques: lever arm cross force at each contact point
+    F, T = s.forces()
+    Ft_i = _KT * xi_ref
+    Fi_ref = -_KN * _DELTA * _N_DIR + Ft_i
+    scale = np.linalg.norm(Fi_ref)
+    assert np.abs(F[0] - Fi_ref).max() <= 1e-11 * scale
+    assert np.abs(F[1] + Fi_ref).max() <= 1e-11 * scale
+    Ti_ref = np.cross(_AI * _N_DIR, Ft_i)
+    Tj_ref = np.cross(-_AJ * _N_DIR, -Ft_i)
+    tscale = np.linalg.norm(Tj_ref)
+    assert np.abs(T[0] - Ti_ref).max() <= 1e-11 * tscale
+    assert np.abs(T[1] - Tj_ref).max() <= 1e-11 * tscale
+    # contact stress (1/V) F_{i<-j} (x) r_ij
+    r = (_AI + _AJ - _DELTA) * _N_DIR
+    sig = s.stress()["contact"]
+    assert np.abs(sig - np.outer(Fi_ref, r) / L ** 3).max() <= 1e-11 * scale * 2.4 / L ** 3
+
+
+@pytest.mark.parametrize("seed", [5, 6, 7])
+def test_rolling_without_slip_stores_no_history(seed):
+    # U_j chosen so that the two contact points move together: the spheres
+    # roll on each other (and translate and spin rigidly); nothing slips
+    rng = np.random.default_rng(seed)
+    W = rng.normal(size=(2, 3))
+    U = np.zeros((2, 3))
+    U[0] = rng.normal(size=3)
+    U[1] = U[0] + np.cross(W[0], _AI * _N_DIR) - np.cross(W[1], -_AJ * _N_DIR)
+    assert np.linalg.norm(_contact_slip(U, W)) <= 1e-14
+    s, _ = _frozen_pair(U, W, mu=1e12)
+    s.step(50)
+    _, hist, contact = s.verlet_list()
+    assert contact[0] == 1
+    vscale = np.abs(U).max() + np.abs(W).max() * _AJ
+    assert np.abs(hist[0]).max() <= 1e-14 * vscale * 50 * _DT * 10
+    F, T = s.forces()
+    assert np.abs(F[0] + _KN * _DELTA * _N_DIR).max() <= 1e-12 * _KN * _DELTA
+    assert np.abs(T).max() <= 1e-12 * _KN * _DELTA
+
+
+def test_capped_friction_opposes_the_slip():
+    # a constant slip drives the spring to the Coulomb cap, after which the
+    # tangential force has magnitude mu k_n delta and the force on j points
+    # against j's slip relative to i
+    mu = 0.5
+    rng = np.random.default_rng(11)
+    U = rng.normal(size=(2, 3))
+    W = rng.normal(size=(2, 3)) * 0.3
+    vt = _contact_slip(U, W)
+    s, _ = _frozen_pair(U, W, mu=mu)
+    cap_len = mu * _KN * _DELTA / _KT
+    t_cap = cap_len / np.linalg.norm(vt)
+    n_before = int(0.5 * t_cap / _DT)
+    s.step(n_before)
+    _, hist, _ = s.verlet_list()
+    assert np.abs(hist[0] - vt * n_before * _DT).max() <= 1e-12 * cap_len
+    s.step(int(2 * t_cap / _DT))                     # well past the cap
+    _, hist, _ = s.verlet_list()
+    F, T = s.forces()
+    Ft_j = F[1] - _KN * _DELTA * _N_DIR              # tangential part on j
+    assert abs(np.dot(Ft_j, _N_DIR)) <= 1e-12 * _KN * _DELTA
+    assert np.linalg.norm(Ft_j) == pytest.approx(mu * _KN * _DELTA, rel=1e-12)
+    # the force on j is antiparallel to j's slip
+    cosang = np.dot(Ft_j, vt) / (np.linalg.norm(Ft_j) * np.linalg.norm(vt))
+    assert cosang == pytest.approx(-1.0, abs=1e-12)
+    assert np.linalg.norm(hist[0]) == pytest.approx(cap_len, rel=1e-12)
+
+
+def _collision_energy_error(dt):
+    """Largest relative change of the mechanical energy of a frictional
+    glancing collision while the spheres touch: translational and
+    rotational kinetic energy of the full-step velocities plus the normal
+    and tangential spring energies."""
+    ai, aj, kn, kt = 1.0, 1.4, 1e4, 5e3
+    rho = 1.0
+    L = 30.0
+    m = 4.0 / 3.0 * math.pi * rho * np.array([ai ** 3, aj ** 3])
+    I = 0.4 * m * np.array([ai ** 2, aj ** 2])
+    # the spheres start touching (overlap 0.004) and approaching, so that the
+    # history starts from zero at t = 0 whatever dt, and the collision ends
+    # when they part
+    c = np.array([1.0, 0.9, -0.4]) / np.linalg.norm([1.0, 0.9, -0.4])
+    x0 = np.array([[12.0, 15.0, 15.0], [12.0, 15.0, 15.0]])
+    x0[1] += (ai + aj - 0.004) * c
+    U0 = np.array([[1.0, 0.1, -0.2], [-1.5, -0.3, 0.4]])
+    W0 = np.array([[0.0, 0.5, -1.0], [0.7, 0.0, 0.3]])
+    s = oracle.System([ai, aj], [L, L, L], kn=kn, kt=kt, mu=1e12, rho=rho,
+                      shear_rate=0.0, kT=0.0, dt=dt, noise=0, lubrication=0,
+                      onebody=0, skin=0.5)
+    s.set_state(x0, U0, W0)
+
+    def energy():
+        x, U, W = s.state()
+        r = x[1] - x[0]
+        d = np.linalg.norm(r)
+        delta = max(ai + aj - d, 0.0)
+        _, hist, contact = s.verlet_list()
+        es = 0.5 * kt * float(np.dot(hist[0], hist[0])) if len(hist) and contact[0] else 0.0
+        ek = 0.5 * np.sum(m[:, None] * U ** 2) + 0.5 * np.sum(I[:, None] * W ** 2)
+        return ek + 0.5 * kn * delta ** 2 + es, delta
+
+    E0, _ = energy()
+    worst, touched, steps = 0.0, 0, 0
+    while steps < int(0.3 / dt):
+        s.step(1)
+        steps += 1
+        E, delta = energy()
+        if delta > 0:
+            touched += 1
+            worst = max(worst, abs(E / E0 - 1.0))
+        elif touched:
+            break
+    _, hist, _ = s.verlet_list()
+    return worst, touched
+
+
+def test_frictional_collision_conserves_energy_as_dt_shrinks():
+    # With lubrication, drag and noise off and an unbounded Coulomb cap the
+    # contact is conservative in continuous time: the tangential spring
+    # stores exactly the work that the friction force and the two contact
+    # torques do on the spheres.  The discrete history update (rotate, then
+    # add the slip of a half-step velocity) is first-order accurate in how the
+    # tangent plane turns, and Velocity-Verlet second-order, so the energy
+    # error of a glancing collision must shrink at least linearly with dt.
+    # A wrong sign of the spin term in the slip, of the tangential force or
+    # of a contact torque, or a wrong lever arm, leaves an O(1) error.
+    errs = []
+    for dt in (2e-4, 1e-4, 5e-5):
+        e, n = _collision_energy_error(dt)
+        errs.append(e)
+        assert n * dt > 0.02          # the spheres stayed in contact for a while
+    assert errs[2] < 5e-6, errs
+    assert errs[0] / errs[1] > 1.8 and errs[1] / errs[2] > 1.8, errs
+
+
+def test_history_turns_with_the_contact_without_changing_length():
+    # Sec. II.A stores the tangential spring displacement xi in the tangent
+    # plane of the contact.  When the contact normal turns while nothing
+    # slips, the stored displacement must turn into the new tangent plane and
+    # keep its length (the spring energy cannot change without slip).  Here
+    # the pair straddles the y boundary of the sheared box: with positions
+    # frozen, the growing tilt of the image turns n by about 0.04 rad over 50
+    # steps, and j moves with exactly the image velocity rate * Ly so that
+    # the contact points do not slip.
+    ai, aj, L, rate = 1.0, 1.4, 20.0, 1.0
+    xi_pos = np.array([10.0, 0.5, 10.0])
+    r0 = np.array([0.05, -2.0, 1.3])                 # min-image r at strain 0
+    r0 *= (ai + aj - 0.01) / np.linalg.norm(r0)
+    xj_pos = xi_pos + r0 + np.array([0.0, L, 0.0])   # j is the image above
+    s = oracle.System([ai, aj], [L, L, L], kn=1e4, kt=5e3, mu=1e12, rho=1e30,
+                      shear_rate=rate, kT=0.0, dt=1e-4, noise=0, lubrication=0,
+                      onebody=0, freeze=1)
+    U = np.zeros((2, 3))
+    U[1, 0] = rate * L
+    W = np.zeros((2, 3))
+    slip = np.array([0.4, 0.3, -0.2])
+    s.set_state(np.stack([xi_pos, xj_pos]), U + np.stack([np.zeros(3), slip]), W)
+    s.step(30)                                      # build up a history
+    s.set_velocities(U, W)                          # from now on nothing slips
+
+    def normal():
+        tilt = s.info()["tilt"]
+        r = xj_pos - xi_pos - np.array([tilt, L, 0.0])
+        return r / np.linalg.norm(r)
+
+    _, h0, c0 = s.verlet_list()
+    n0 = normal()
+    assert c0[0] == 1 and abs(np.dot(h0[0], n0)) <= 1e-14 * np.linalg.norm(h0[0])
+    s.step(50)
+    _, h1, c1 = s.verlet_list()
+    n1 = normal()
+    theta = math.acos(min(1.0, float(np.dot(n0, n1))))
+    assert c1[0] == 1 and theta > 0.03
+    xi0, xi1 = h0[0], h1[0]
+    assert np.linalg.norm(xi0) > 1e-4
+    assert np.linalg.norm(xi1) == pytest.approx(np.linalg.norm(xi0), rel=1e-13)
+    assert abs(np.dot(xi1, n1)) <= 1e-13 * np.linalg.norm(xi1)
+    # it turned with the contact: the rotation taking n0 to n1 takes xi0 to
+    # xi1 up to the O(theta^2) by which stepwise turning differs from it
+    k = np.cross(n0, n1)
+    k /= np.linalg.norm(k)
+    rot = (xi0 * math.cos(theta) + np.cross(k, xi0) * math.sin(theta)
+           + k * np.dot(k, xi0) * (1 - math.cos(theta)))
+    assert np.linalg.norm(xi1 - rot) <= theta ** 2 * np.linalg.norm(xi0)
