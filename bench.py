@@ -156,29 +156,41 @@ class Clocks:
 # algorithmic bytes per sphere of each kernel family
 # ---------------------------------------------------------------------------
 def algorithmic_bytes(family: str, precision: str, K: float, c: float, fric: bool) -> float:
-    """Bytes each launch must move per sphere: every record read or written
-    once, gathers of neighbours not counted again, atomics counted as one
-    write of the accumulator.  K = half-list slots per sphere, c = touching
-    pairs with history per sphere."""
+    """Bytes a launch must move per sphere for the method's work: every record
+    read or written once, gathers of neighbours not counted again.  K =
+    half-list slots per sphere, c = touching pairs with history per sphere.
+
+    Pair kernel: FP64 128 + 4K + 48c (own x, U, Omega 72 + radius 4, row
+    length 4 + list 4K, F and T written 48, history 48 per touching pair read
+    and written); mixed 100 + 4K + 48c (three 16-byte single-precision
+    mirrors instead of the FP64 records).  Integrator: FP64 196 (read x, U,
+    Omega, F, T 120 + radius 4, write x, U, Omega 72), mixed 244 (plus three
+    16-byte mirrors written)."""
+    hist = 48.0 * c if fric else 0.0
+    if family == "pair":
+        if precision == "mixed":
+            return 48.0 + 4.0 + 4.0 * K + 48.0 + hist
+        return 76.0 + 4.0 + 4.0 * K + 48.0 + hist
+    if family == "integrate":
+        return 244.0 if precision == "mixed" else 196.0
+    return 0.0
+
+
+def layout_bytes(family: str, precision: str, K: float, c: float, fric: bool) -> float:
+    """Bytes the library's own layout moves per sphere in a launch (what the
+    DRAM traffic is compared with): the mixed path's double-float position
+    records (32 B with the low words), velocity + tag and spin + packed cell
+    (16 B each), float4 force and torque accumulators (32 B), and the 64-bit
+    contact mask (16 B read and written) beside the 32-byte history records."""
     hist = (16.0 + 48.0 * c) if fric else 0.0
     if family == "pair":
         if precision == "mixed":
-            # own mirrors: double-float offset+radius (32), velocity+tag (16),
-            # spin+cell (16); row length (4) + list 4K; float4 force and
-            # torque accumulation (32); contact mask / history
             return 64.0 + 4.0 + 4.0 * K + 32.0 + hist
-        # x, U, W records (96) + tag, row length (8) + list 4K + force and
-        # torque accumulation (48) + contact mask / history
         return 96.0 + 8.0 + 4.0 * K + 48.0 + hist
     if family == "integrate":
         if precision == "mixed":
-            # read x, U, W (96) + float4 F, T (32) + cell, tag (8); write
-            # x, U, W (96) + mirrors (64) + cleared F, T (32)
             return 96.0 + 32.0 + 8.0 + 96.0 + 64.0 + 32.0
-        # read x, U, W (96) + F, T (48); write x, U, W (96) + cleared F, T (48)
         return 96.0 + 48.0 + 96.0 + 48.0
-    if family == "finalize":
-        return 32.0 + 32.0 + 48.0 + 32.0 + 32.0
     return 0.0
 
 
@@ -270,6 +282,7 @@ def run_ours(args, rank, world, local_rank, dist):
               key=lambda f: prof[f]["ms"])
     hbm, peak_kind = peaks()
     per_sphere = algorithmic_bytes(fam, args.precision, K, c, fric)
+    per_sphere_layout = layout_bytes(fam, args.precision, K, c, fric)
     roofline = None
     if per_sphere > 0 and prof[fam]["launches"] > 0:
         bytes_per_launch = per_sphere * N
@@ -291,6 +304,7 @@ def run_ours(args, rank, world, local_rank, dist):
                     "frac": round(achieved / hbm, 4), "traffic": traffic,
                     "algorithmic_bytes_per_launch": bytes_per_launch,
                     "bytes_per_sphere": per_sphere,
+                    "layout_bytes_per_sphere": round(per_sphere_layout, 3),
                     "ms_per_launch": prof[fam]["ms_per_launch"],
                     "half_list_slots_per_sphere": round(K, 3),
                     "contacts_per_sphere": round(c, 3)}
@@ -365,7 +379,7 @@ def run_ours(args, rank, world, local_rank, dist):
         "metric": METRIC, "value": round(value, 1), "unit": METRIC,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32-pair/f64-state"
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32-pair/df32x2-state/f32-warp-virials"
         if args.precision == "mixed" else "f64",
         "data": "synthetic seeded packing (no dataset)",
         "config": {"workload": WORKLOAD, "N": N, "phi": 0.58, "Pe": 1000.0, "mu": 1.0,

@@ -56,14 +56,19 @@ extern "C" {
 #define SUSP_ESTATE 4    /* call order (e.g. step before set_state)         */
 #define SUSP_ENEIGH 5    /* neighbour row exceeded its capacity             */
 #define SUSP_EUNSTABLE 6 /* non-finite position/velocity or runaway overlap */
-#define SUSP_ETIMEOUT 7  /* a bounded device wait gave up                   */
+                         /* 7 is not used: no call waits on the device      */
+                         /* with a time limit                               */
 #define SUSP_ENODEV 8    /* no CUDA device is visible                       */
 
 /* ---- parameters --------------------------------------------------------- */
 #define SUSP_FP64 0  /* every step in double precision                      */
 #define SUSP_MIXED 1 /* pair arithmetic in single precision on gaps formed  */
-                     /* from double positions; integration, tangential      */
-                     /* history and stress accumulation in double           */
+                     /* from double-float positions (pairs of floats, a    */
+                     /* 48-bit significand); positions, velocities and the */
+                     /* tangential history kept and integrated in          */
+                     /* double-float; per-warp virial sums in single       */
+                     /* precision, folded per block and summed over blocks */
+                     /* and time in double                                 */
 
 typedef struct susp_params {
   double eta;         /* liquid viscosity                                   */
@@ -93,19 +98,30 @@ typedef struct susp_params {
   int32_t structural; /* 1: sample the structural Brownian stress (Eq. 26)  */
   int32_t series_cap; /* per replica, samples of Sigma^B_xy kept for        */
                       /* Green-Kubo (0: none); needs structural = 1         */
-  int32_t reserved;
+  int32_t rebuild_every; /* n > 0: rebuild the neighbour list at least every */
+                      /* n steps (the displacement bound of the skin may    */
+                      /* rebuild sooner); 0: only when that bound requires  */
   double rep_A;       /* repulsion force scale A of Eq. 34 (0: off);        */
                       /* batch handles: this replica's A                    */
   double rep_cut;     /* repulsion acts for h <= rep_cut kappa,             */
                       /* kappa = 0.01 (a_i + a_j) (default 10)              */
   double shell;       /* structural shell Delta / a_i (paper: 0.05)         */
+  int32_t deterministic; /* must be 0: force sums use atomics, so their     */
+                      /* order (and the last bits) may change from run to   */
+                      /* run; the stress reductions are always in a fixed   */
+                      /* order                                              */
+  int32_t autotune;   /* 1: the first step call of the handle runs          */
+                      /* susp_autotune() over the skins 0.2, 0.3, 0.45,    */
+                      /* 0.6 and 0.8 (100 trial steps each) and keeps the  */
+                      /* fastest                                            */
 } susp_params;
 
 /* Fills *p with the defaults: eta = rho = 1, kn = 1e4, kt = 0, mu = 0,
  * xi_min = 1e-3, xi_max = 0.05, skin = 0.3, shear_rate = 1, kT = 0,
  * torque_sign = -1, dt = 1e-4, seed = 0, FP64, all terms on, sample_every = 1,
  * kmax = 48, autotuned threads per particle, graphs on, no repulsion
- * (rep_A = 0, rep_cut = 10), no structural stress (shell = 0.05), no series. */
+ * (rep_A = 0, rep_cut = 10), no structural stress (shell = 0.05), no series,
+ * rebuild_every = 0, deterministic = 0, autotune = 0. */
 void susp_default_params(susp_params* p);
 
 typedef struct susp_s susp_t;
@@ -249,7 +265,7 @@ int susp_profile(susp_t* h, int64_t n_steps, double dt, double* out);
  *            sum_{j: h_ij <= Delta} n_ij n_ij with Delta = shell a_i, overlaps
  *            included (zero unless structural = 1; not added to eta_r) */
 #define SUSP_STRESS_LEN 76
-int susp_stress(susp_t* h, int32_t replica, double* out);
+int susp_stress(susp_t* h, double* out, int32_t replica);
 
 /* The current half neighbour list as tag pairs ij[count][2] with i < j in
  * lexicographic order; *count receives the number of pairs, at most cap are

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsusp.so")
 
 SUSP_OK, SUSP_EINVAL, SUSP_ENOMEM, SUSP_ECUDA, SUSP_ESTATE = 0, 1, 2, 3, 4
-SUSP_ENEIGH, SUSP_EUNSTABLE, SUSP_ETIMEOUT, SUSP_ENODEV = 5, 6, 7, 8
+SUSP_ENEIGH, SUSP_EUNSTABLE, SUSP_ENODEV = 5, 6, 8
 SUSP_FP64, SUSP_MIXED = 0, 1
 SUSP_STRESS_LEN = 76
 SUSP_INFO_LEN = 14
@@ -26,7 +26,7 @@ PROFILE_FAMILIES = ("integrate", "rebuild", "pair", "reduce", "finalize")
 
 ERROR_NAMES = {0: "SUSP_OK", 1: "SUSP_EINVAL", 2: "SUSP_ENOMEM", 3: "SUSP_ECUDA",
                4: "SUSP_ESTATE", 5: "SUSP_ENEIGH", 6: "SUSP_EUNSTABLE",
-               7: "SUSP_ETIMEOUT", 8: "SUSP_ENODEV"}
+               8: "SUSP_ENODEV"}
 
 
 class SuspError(RuntimeError):
@@ -48,8 +48,9 @@ class susp_params(C.Structure):
         ("contact", C.c_int32), ("sample_every", C.c_int32),
         ("kmax", C.c_int32), ("threads_per_particle", C.c_int32),
         ("use_graphs", C.c_int32), ("structural", C.c_int32),
-        ("series_cap", C.c_int32), ("reserved", C.c_int32),
+        ("series_cap", C.c_int32), ("rebuild_every", C.c_int32),
         ("rep_A", C.c_double), ("rep_cut", C.c_double), ("shell", C.c_double),
+        ("deterministic", C.c_int32), ("autotune", C.c_int32),
     ]
 
 
@@ -79,7 +80,7 @@ _SIGNATURES = {
     "susp_step": (C.c_int, [_H, C.c_int64, C.c_double, C.c_double, C.c_double,
                             C.c_uint64]),
     "susp_step_batch": (C.c_int, [_H, C.c_int64, C.c_double]),
-    "susp_stress": (C.c_int, [_H, C.c_int32, _D]),
+    "susp_stress": (C.c_int, [_H, _D, C.c_int32]),
     "susp_profile": (C.c_int, [_H, C.c_int64, C.c_double, _D]),
     "susp_get_pairs": (C.c_int, [_H, _I32, C.c_int64, _I64]),
     "susp_get_history": (C.c_int, [_H, _I32, _D, C.c_int64, _I64]),
@@ -150,6 +151,27 @@ def green_kubo(x, max_lag: int, dt: float, V: float, kT: float):
     return Cc, eta, (float(fit[0]), float(fit[1]))
 
 
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+def torch_allocator(device=None):
+    """(alloc, release) callables that take device memory from PyTorch's
+    caching allocator on `device` (default: the current device), for
+    ``System.set_allocator``."""
+    import torch
+
+    dev = torch.cuda.current_device() if device is None else torch.device(device).index
+
+    def alloc(nbytes):
+        return int(torch.cuda.caching_allocator_alloc(int(nbytes), dev))
+
+    def release(ptr):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return alloc, release
+
+
 def check(code: int, h=None):
     if code != SUSP_OK:
         msg = lib.susp_last_error(h).decode() if h else lib.susp_create_error().decode()
@@ -210,6 +232,23 @@ class System:
     def set_stream(self, stream_ptr: int):
         self._chk(lib.susp_set_stream(self._h, C.c_void_p(stream_ptr)))
 
+    def set_allocator(self, alloc, release):
+        """Device memory of this handle from alloc(nbytes) -> pointer and
+        back through release(pointer); before the first set_state."""
+        def a(n, _ctx):
+            try:
+                return alloc(n) or None
+            except Exception:
+                return None
+
+        def r(ptr, _ctx):
+            release(ptr)
+
+        # the C callbacks must outlive the handle
+        self._allocator = (_ALLOC_FN(a), _FREE_FN(r))
+        self._chk(lib.susp_set_allocator(self._h, C.cast(self._allocator[0], C.c_void_p),
+                                         C.cast(self._allocator[1], C.c_void_p), None))
+
     # -- state --------------------------------------------------------------
     def set_state(self, x, U=None, W=None):
         x, U, W = _vec(x, self.N), _vec(U, self.N), _vec(W, self.N)
@@ -256,7 +295,7 @@ class System:
 
     def stress(self, replica: int = 0) -> dict:
         out = np.zeros(SUSP_STRESS_LEN)
-        self._chk(lib.susp_stress(self._h, int(replica), _dp(out)))
+        self._chk(lib.susp_stress(self._h, _dp(out), int(replica)))
         t = out[:54].reshape(6, 3, 3)
         return dict(contact=t[0], lubrication=t[1], brownian=t[2], drag=t[3],
                     kinetic=t[4], kinetic_rot=t[5], eta_r=out[54], N1=out[55],

@@ -83,6 +83,7 @@ struct susp_s {
   int last_nbuilds_seen = 0;
   // profiling: events around each launch, summed per kernel family
   bool profiling = false;
+  bool autotuned = false;  // the autotune parameter's one tuning pass is done
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_marks;
@@ -148,6 +149,13 @@ int validate_params(const susp_params* p, std::string& msg) {
   if (p->structural != 0 && p->structural != 1) { msg = "structural must be 0 or 1"; return SUSP_EINVAL; }
   if (p->series_cap < 0) { msg = "series_cap must be >= 0"; return SUSP_EINVAL; }
   if (p->series_cap > 0 && !p->structural) { msg = "series_cap needs structural = 1"; return SUSP_EINVAL; }
+  if (p->rebuild_every < 0) { msg = "rebuild_every must be >= 0"; return SUSP_EINVAL; }
+  if (p->deterministic != 0) {
+    msg = "deterministic = 1 is not offered: the force sums use atomics (the stress "
+          "reductions are in a fixed order)";
+    return SUSP_EINVAL;
+  }
+  if (p->autotune != 0 && p->autotune != 1) { msg = "autotune must be 0 or 1"; return SUSP_EINVAL; }
   const int t = p->threads_per_particle;
   if (!(t == 0 || t == 1 || t == 2 || t == 4 || t == 8)) {
     msg = "threads_per_particle must be 0, 1, 2, 4 or 8"; return SUSP_EINVAL;
@@ -451,6 +459,7 @@ StepArgs make_args(const susp_t* h, double dt, int advance, int sample) {
   for (const Replica& R : h->repl_h) rep_on |= R.rep_A > 0.0;
   s.rep_on = rep_on;
   s.structural = p.structural;
+  s.rebuild_every = p.rebuild_every;
   s.rep_fac = 1.0 + 0.01 * p.rep_cut;
   s.rep_cut = p.rep_cut;
   s.rep_hc = 0.01 * p.rep_cut;
@@ -839,7 +848,7 @@ int set_state_impl(susp_t* h, const double* x, const double* U, const double* W,
 // checkpoints
 // ---------------------------------------------------------------------------
 // File layout (native byte order, written by this library only):
-//   "SUSPCKP2", int64 N, int32 R, int32 precision, int64 k, int64 steps_done,
+//   "SUSPCKP3", int64 N, int32 R, int32 precision, int64 k, int64 steps_done,
 //   double last_dt, int32 forces_valid, int32 0,
 //   R x susp_params, R x double strain, N x double radius,
 //   5 x [N][3] double: x, U, Omega, F, T (tag order),
@@ -847,7 +856,7 @@ int set_state_impl(susp_t* h, const double* x, const double* U, const double* W,
 //   int64 npairs, npairs x (int32 tag_i, int32 tag_j), npairs x 3 double xi_t,
 //   "SUSPEND1".
 // The mixed layout's double-float values convert to and from double exactly.
-constexpr char kCkMagic[8] = {'S', 'U', 'S', 'P', 'C', 'K', 'P', '2'};
+constexpr char kCkMagic[8] = {'S', 'U', 'S', 'P', 'C', 'K', 'P', '3'};
 constexpr char kCkEnd[8] = {'S', 'U', 'S', 'P', 'E', 'N', 'D', '1'};
 
 struct CkHeader {
@@ -1227,6 +1236,9 @@ void susp_default_params(susp_params* p) {
   p->rep_A = 0.0;
   p->rep_cut = 10.0;
   p->shell = 0.05;
+  p->rebuild_every = 0;
+  p->deterministic = 0;
+  p->autotune = 0;
 }
 
 int susp_create(susp_t** out, int64_t N, const double* radii, const double box[3],
@@ -1355,6 +1367,20 @@ int susp_evaluate(susp_t* h) {
   return check_errors(h);
 }
 
+int susp_autotune(susp_t* h, int64_t trial_steps, double dt, const double* skins, int32_t n,
+                  double* ms_per_step, double* chosen);
+
+// With the autotune parameter set, the first step call of a handle picks the
+// skin among a fixed set of candidates (the tuning leaves the state as it
+// was).
+static int autotune_once(susp_t* h, double dt) {
+  if (!h->p0.autotune || h->autotuned || !h->have_state) return SUSP_OK;
+  h->autotuned = true;
+  const double skins[5] = {0.2, 0.3, 0.45, 0.6, 0.8};
+  double chosen = 0.0;
+  return susp_autotune(h, 100, dt, skins, 5, nullptr, &chosen);
+}
+
 int susp_step(susp_t* h, int64_t n_steps, double shear_rate, double kT, double dt,
               uint64_t seed) {
   if (!h) return SUSP_EINVAL;
@@ -1378,14 +1404,16 @@ int susp_step(susp_t* h, int64_t n_steps, double shear_rate, double kT, double d
     drop_graphs(h);
   }
   if (dt != h->last_dt && h->last_dt > 0) h->forces_valid = false;
-  return run_steps(h, n_steps, dt);
+  int rc = autotune_once(h, dt);
+  return rc ? rc : run_steps(h, n_steps, dt);
 }
 
 int susp_step_batch(susp_t* h, int64_t n_steps, double dt) {
   if (!h) return SUSP_EINVAL;
   h->err.clear();
   if (dt != h->last_dt && h->last_dt > 0) h->forces_valid = false;
-  return run_steps(h, n_steps, dt);
+  int rc = autotune_once(h, dt);
+  return rc ? rc : run_steps(h, n_steps, dt);
 }
 
 int susp_profile(susp_t* h, int64_t n_steps, double dt, double* out) {
@@ -1417,7 +1445,7 @@ int susp_profile(susp_t* h, int64_t n_steps, double dt, double* out) {
   return SUSP_OK;
 }
 
-int susp_stress(susp_t* h, int32_t replica, double* out) {
+int susp_stress(susp_t* h, double* out, int32_t replica) {
   if (!h || !out) return SUSP_EINVAL;
   if (replica < 0 || replica >= h->R) return fail(h, SUSP_EINVAL, "replica out of range");
   if (!h->allocated) return fail(h, SUSP_ESTATE, "no state yet");

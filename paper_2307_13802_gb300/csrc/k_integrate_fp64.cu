@@ -61,6 +61,8 @@ __device__ void integrator_epilogue(const Arrays& A, const StepArgs& s,
   const double D = ctl->disp_bound;
   const double drift = 2.0 * D + s.rate_max * ctl->t_since_build * (s.rcmax + 2.0 * D);
   if (drift >= s.skin) ctl->need_rebuild = 1;
+  ctl->steps_since_build = ctl->steps_since_build + 1;
+  if (s.rebuild_every > 0 && ctl->steps_since_build >= s.rebuild_every) ctl->need_rebuild = 1;
   if (use_cond) {
     cudaGraphSetConditional((cudaGraphConditionalHandle)cond_handle,
                             ctl->need_rebuild ? 1u : 0u);

@@ -405,6 +405,7 @@ __global__ void k_finish(Arrays A) {
   ctl->need_rebuild = 0;
   ctl->disp_bound = 0.0;
   ctl->t_since_build = 0.0;
+  ctl->steps_since_build = 0;
   ctl->nbuilds = ctl->nbuilds + 1;
 }
 

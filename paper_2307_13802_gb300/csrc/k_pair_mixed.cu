@@ -21,8 +21,9 @@
 //     sector), updated with error-free FP32 transformations (dfloat.cuh), so
 //     it accumulates with a 48-bit significand.
 //   - Stresses: single-precision virials summed over the warp batch by batch
-//     (a reduce-scatter leaves entry l in lane l), block sums in single
-//     precision, global and time sums in double.
+//     (a reduce-scatter leaves entry l in lane l); the warp sums are folded
+//     into the block partial in double, and the sums over blocks, replicas
+//     and time are double as well.
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
@@ -603,10 +604,10 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   }
   if (SAMPLE) {
     // single-precision warp sums into shared memory; the last warp of the
-    // block to arrive folds the eight warp sums (in warp order) into the
-    // block partial, so no warp waits at a block-wide barrier.  Blocks,
-    // replicas and time are summed in double by the next pair launch (or the
-    // reduction kernels at the end of a call).
+    // block to arrive folds the eight warp sums (in warp order, in double)
+    // into the block partial, so no warp waits at a block-wide barrier.
+    // Blocks, replicas and time are summed in double by the next pair launch
+    // (or the reduction kernels at the end of a call).
     if (lane < kVirLen) sW[warp * kPartialLen + lane] = vacc;
     __syncwarp();
     __threadfence_block();
@@ -620,9 +621,9 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
       constexpr int kSym[9] = {0, 1, 2, 1, 3, 4, 2, 4, 5};
       for (int cc = lane; cc < kPartialLen; cc += 32) {
         const int src = cc < kStrOff ? cc : kStrOff + kSym[cc - kStrOff];
-        float sum = 0.0f;
+        double sum = 0.0;
         for (int w = 0; w < kBlock / 32; ++w)
-          sum += *(volatile float*)&sW[w * kPartialLen + src];
+          sum += (double)*(volatile float*)&sW[w * kPartialLen + src];
         A.pair_partial_w[((int64_t)s.ppar * gridDim.x + b) * kPartialLen + cc] = sum;
       }
     }

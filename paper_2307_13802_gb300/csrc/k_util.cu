@@ -139,7 +139,7 @@ __global__ void k_row_counts(Arrays A, int with_history, long long* __restrict__
 
 // The two levels of the stress reduction as kernels of their own: one block
 // per chunk, then one block per replica (reduce.cuh gives the order).
-__global__ void __launch_bounds__(256) k_reduce_chunks(Arrays A, const float* pw,
+__global__ void __launch_bounds__(256) k_reduce_chunks(Arrays A, const double* pw,
                                                        int sample_pair, int sample_kin) {
   __shared__ double part[4][64];
   reduce_chunk(A, blockIdx.x, pw, sample_pair, sample_kin, part);
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(256) k_reduce_replicas(Arrays A, int sample_pa
 void launch_reduce_stress(const Arrays& A, const BlockMap& bm, int sample_pair,
                           int sample_kin, int ppar, cudaStream_t st) {
   if (!sample_pair && !sample_kin) return;
-  const float* pw = A.pair_partial_w + (int64_t)ppar * bm.nblocks * kPartialLen;
+  const double* pw = A.pair_partial_w + (int64_t)ppar * bm.nblocks * kPartialLen;
   k_reduce_chunks<<<A.nchunk, 256, 0, st>>>(A, pw, sample_pair, sample_kin);
   k_reduce_replicas<<<A.R, 256, 0, st>>>(A, sample_pair, sample_kin);
 }

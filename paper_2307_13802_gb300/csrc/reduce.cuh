@@ -19,9 +19,9 @@ static_assert(kRedLen <= 64, "one thread per component and row group");
 // the 4 x 64 layout sums component c over rows g, g + 4, ... of the chunk
 // (coalesced rows of block partials), and the four row sums are added in
 // order g = 0..3.  Each thread issues all its loads before the first add
-// (rows past the chunk's end read as +0).  pw: the single-precision pair
-// partials of the mixed path (one of the two buffers).
-__device__ __forceinline__ void reduce_chunk(const Arrays& A, int ch, const float* pw,
+// (rows past the chunk's end read as +0).  pw: the pair partials of the
+// mixed path (one of the two buffers).
+__device__ __forceinline__ void reduce_chunk(const Arrays& A, int ch, const double* pw,
                                              int sample_pair, int sample_kin,
                                              double (&part)[4][64]) {
   const int g = threadIdx.x >> 6, c = threadIdx.x & 63;
@@ -33,7 +33,7 @@ __device__ __forceinline__ void reduce_chunk(const Arrays& A, int ch, const floa
 #pragma unroll
       for (int k = 0; k < kRows; ++k) {
         const int b = b0 + g + 4 * k;
-        v[k] = b < b1 ? (double)__ldcg(pw + (int64_t)b * kPartialLen + c) : 0.0;
+        v[k] = b < b1 ? __ldcg(pw + (int64_t)b * kPartialLen + c) : 0.0;
       }
     } else {
 #pragma unroll
@@ -114,7 +114,7 @@ __device__ __forceinline__ void reduce_replica(const Arrays& A, int r, int sampl
 // before the arrival; the last arrival fences, sums the replica and resets
 // the counter for the next launch.
 __device__ __forceinline__ void reduce_chunk_then_replica(const Arrays& A, int ch,
-                                                          const float* pw, int sample_pair,
+                                                          const double* pw, int sample_pair,
                                                           int sample_kin) {
   __shared__ double part[4][64];
   __shared__ unsigned int s_last;

@@ -135,6 +135,7 @@ struct Ctl {
   unsigned int vmax_fbits;      // same, single precision bits (mixed path)
   double disp_bound;            // accumulated displacement bound D
   double t_since_build;
+  long long steps_since_build;
   int need_rebuild;
   int err;
   int cur;                      // live copy of the double-buffered arrays
@@ -193,9 +194,10 @@ struct Arrays {
   int64_t ncell;
   // reductions
   double* pair_partial; // [nblocks][27]
-  float* pair_partial_w; // [2][nblocks][45] single-precision (mixed path): two
-                         // buffers, so that a pair launch can reduce the
-                         // previous launch's partials while writing its own
+  double* pair_partial_w; // [2][nblocks][45] block partials of the mixed path
+                          // (single-precision warp sums folded in double): two
+                          // buffers, so that a pair launch can reduce the
+                          // previous launch's partials while writing its own
   double* kin_partial;  // [nblocks][18]
   double* stress_acc;   // [R][kAccStride]: 45 pair, 18 kinetic, pair / kinetic counts
   double* series;       // [R][series_cap] Sigma^B_xy per sampled evaluation
@@ -229,6 +231,7 @@ struct StepArgs {
   int noise, lubrication, onebody, contact, friction;
   int rep_on;        // some replica has repulsion (Eq. 34)
   int structural;    // structural Brownian sums (Eq. 26) on sampled steps
+  int rebuild_every; // > 0: rebuild at least every this many steps
   double rep_fac;    // 1 + 0.01 rep_cut: repulsion range over a_i + a_j
   double rep_cut;    // repulsion for h <= rep_cut kappa, kappa = 0.01 (a_i + a_j)
   double rep_hc;     // 0.01 rep_cut: repulsion gap cutoff over a_i + a_j

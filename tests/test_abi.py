@@ -68,3 +68,41 @@ def test_green_kubo_argument_errors_need_no_device():
             assert e.code == s.SUSP_EINVAL
         else:
             raise AssertionError(f"accepted {args[1:]}")
+
+
+def test_params_struct_layout_matches_the_header(tmp_path):
+    # the binding's ctypes mirror of susp_params has the C layout: compile a
+    # probe against include/susp.h that prints sizeof and every offsetof
+    import subprocess
+
+    import paper_2307_13802_gb300 as s
+
+    fields = [f for f, _ in s.susp_params._fields_]
+    src = tmp_path / "probe.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "susp.h"\nint main(void){\n'
+        '  printf("%zu\\n", sizeof(susp_params));\n'
+        + "".join(f'  printf("%zu\\n", offsetof(susp_params, {f}));\n' for f in fields)
+        + "  return 0;\n}\n")
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(s.susp_params)
+    for f, off in zip(fields, out[1:]):
+        assert getattr(s.susp_params, f).offset == off, f
+
+
+def test_parameters_are_checked_before_any_device_work():
+    # invalid parameters are reported as SUSP_EINVAL with or without a GPU
+    import paper_2307_13802_gb300 as s
+
+    for bad in (dict(deterministic=1), dict(rebuild_every=-1), dict(autotune=2),
+                dict(sample_every=0), dict(xi_min=0.1, xi_max=0.05)):
+        try:
+            s.System([1.0] * 10, [30.0, 30.0, 30.0], **bad)
+        except s.SuspError as e:
+            assert e.code == s.SUSP_EINVAL, bad
+        else:
+            raise AssertionError(f"accepted {bad}")

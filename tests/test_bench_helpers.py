@@ -47,17 +47,21 @@ def test_source_hash_follows_every_included_header(tree):
 
 
 def test_algorithmic_bytes_per_sphere():
+    # the method's work per sphere: mixed pair 100 + 4K + 48c, FP64 pair
+    # 128 + 4K + 48c; integrators 244 (mixed) and 196 (FP64)
     K, c = 3.943, 1.894
-    # mixed pair kernel: own mirrors 64, row length 4, list 4K, float4 force and
-    # torque 32, contact mask 16, history record read and written 48 per contact
     assert bench.algorithmic_bytes("pair", "mixed", K, c, True) == pytest.approx(
-        64 + 4 + 4 * K + 32 + 16 + 48 * c)
+        100 + 4 * K + 48 * c)
     assert bench.algorithmic_bytes("pair", "mixed", K, c, False) == pytest.approx(
-        64 + 4 + 4 * K + 32)
+        100 + 4 * K)
     assert bench.algorithmic_bytes("pair", "fp64", K, c, True) == pytest.approx(
-        96 + 8 + 4 * K + 48 + 16 + 48 * c)
-    assert bench.algorithmic_bytes("integrate", "mixed", K, c, True) == 328.0
-    assert bench.algorithmic_bytes("integrate", "fp64", K, c, True) == 288.0
+        128 + 4 * K + 48 * c)
+    assert bench.algorithmic_bytes("integrate", "mixed", K, c, True) == 244.0
+    assert bench.algorithmic_bytes("integrate", "fp64", K, c, True) == 196.0
+    # the library's own layout: mixed pair 64 + 4 + 4K + 32 + 16 + 48c
+    assert bench.layout_bytes("pair", "mixed", K, c, True) == pytest.approx(
+        64 + 4 + 4 * K + 32 + 16 + 48 * c)
+    assert bench.layout_bytes("integrate", "mixed", K, c, True) == 328.0
 
 
 class _Proc:
