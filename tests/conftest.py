@@ -20,3 +20,29 @@ def _build_cpu_helpers():
     import workloads
     oracle.build()
     workloads.build()
+
+
+# Measured errors of the parity tests, written as JSON lines to the file
+# named by SUSP_MEASURE_LOG (if set) when the session ends, so that each bar
+# can be set to a stated multiple of the error it guards.
+_MEASURED = []
+
+
+@pytest.fixture
+def record(request):
+    def rec(name, value, bar=None):
+        _MEASURED.append(dict(test=request.node.nodeid, name=name,
+                              value=float(value),
+                              bar=None if bar is None else float(bar)))
+    return rec
+
+
+def pytest_sessionfinish(session, exitstatus):
+    path = os.environ.get("SUSP_MEASURE_LOG")
+    if not path or not _MEASURED:
+        return
+    import json
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    with open(path, "a") as f:
+        for m in _MEASURED:
+            f.write(json.dumps(m) + "\n")

@@ -79,3 +79,28 @@ def test_autotune_restores_the_state(precision):
     assert np.abs(xa - xb).max() <= (1e-10 if precision == "fp64" else 1e-6)
     sa, sb = a.stress(), b.stress()
     assert sa["samples"] == sb["samples"] == 200
+
+
+def test_rebuild_every_and_autotune_parameters(record):
+    # rebuild_every = n rebuilds the list at least every n steps, and a
+    # rebuild keeps the physics; autotune = 1 tunes the skin on the first
+    # step call and leaves the run as it would have been (FP64: the forces of
+    # the three runs agree to the summation order of the atomics)
+    import paper_2307_13802_gb300 as susp
+
+    w = workloads.make(1500, 0.55, 100.0, 1.0, pack_seed=67, dyn_seed=68)
+    p = w.params
+    runs = {}
+    for name, extra in (("plain", {}), ("every10", dict(rebuild_every=10)),
+                        ("tuned", dict(autotune=1))):
+        g = susp.System(w.radii, w.box, **_args(w), **extra)
+        g.set_state(w.x, w.U, w.W)
+        g.step(200, p["shear_rate"], p["kT"], p["dt"], p["seed"])
+        runs[name] = (g.forces()[0], g.info(), g.stress())
+    F0, i0, s0 = runs["plain"]
+    assert runs["every10"][1]["nbuilds"] >= 20 > i0["nbuilds"]
+    for name in ("every10", "tuned"):
+        F, info, s = runs[name]
+        record(f"{name}_force", _relerr(F, F0), 1e-9)
+        assert _relerr(F, F0) <= 1e-9, name
+        assert info["k"] == i0["k"] and s["samples"] == s0["samples"] == 200

@@ -6,7 +6,10 @@ The replicas share kernels and launches but no data: each has its own box,
 cell grid, strain, noise key and stress sums, and its particles are never
 paired with another replica's.  The per-replica results therefore equal
 those of separate handles up to the order of the force sums (atomics), the
-same bar as two runs of one handle."""
+same bar as two runs of one handle.  Bars are 10-30 times the largest
+difference measured on a GB300 over 200 steps: FP64 x 8e-15, U 1.4e-13,
+F 2.4e-13; mixed (single-precision force atomics) x 2.5e-8, U 2.5e-7,
+F 8e-7 of the largest entry."""
 import numpy as np
 import pytest
 
@@ -18,7 +21,7 @@ ROWS = [dict(N=300, phi=0.45, pe=1000.0, mu=0.0, seed=71),
         dict(N=520, phi=0.55, pe=10.0, mu=1.0, seed=72),
         dict(N=410, phi=0.50, pe=0.5, mu=0.5, seed=73)]
 # (x absolute, U relative to its largest entry, F normwise)
-TOL = {"fp64": (1e-10, 1e-9, 1e-9), "mixed": (1e-6, 1e-5, 1e-3)}
+TOL = {"fp64": (1e-13, 3e-12, 5e-12), "mixed": (5e-7, 5e-6, 1e-5)}
 
 
 def _kw(w, precision):
@@ -30,7 +33,7 @@ def _kw(w, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batch_equals_separate_handles(precision):
+def test_batch_equals_separate_handles(precision, record):
     import paper_2307_13802_gb300 as susp
 
     ws = [workloads.make(r["N"], r["phi"], r["pe"], r["mu"], pack_seed=700 + i,
@@ -54,6 +57,10 @@ def test_batch_equals_separate_handles(precision):
         x, U, W = g.state()
         F, T = g.forces()
         sl = slice(off[r], off[r + 1])
+        record(f"r{r}_x", np.abs(xb[sl] - x).max(), tx)
+        record(f"r{r}_U", np.abs(Ub[sl] - U).max() / np.abs(U).max(), tu)
+        record(f"r{r}_F", np.abs(Fb[sl] - F).max() / np.abs(F).max(), tf)
+        record(f"r{r}_T", np.abs(Tb[sl] - T).max() / np.abs(T).max(), tf)
         assert np.abs(xb[sl] - x).max() <= tx, r
         assert np.abs(Ub[sl] - U).max() <= tu * np.abs(U).max(), r
         assert np.abs(Fb[sl] - F).max() <= tf * np.abs(F).max(), r

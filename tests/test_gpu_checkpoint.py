@@ -7,7 +7,10 @@ run repeats the same arithmetic.  The force sums (atomics) may add in another
 order, so the two runs agree to rounding grown over the remaining steps, not
 bitwise.  A restore that dropped any of those parts would be off by far
 more: the opening half kick of the resumed step moves U by dt F / m ~ 1e-4,
-a lost tangential history changes contact forces at O(1)."""
+a lost tangential history changes contact forces at O(1).  Bars are 10-30
+times the largest difference measured over two runs on a GB300 (FP64: x
+8.9e-16, U 3.4e-14, W 8.6e-15, F 2.0e-14, history 1.4e-15; mixed: x
+5.6e-10, U 1.1e-7, F 1.2e-7, history 5.6e-9)."""
 import numpy as np
 import pytest
 
@@ -16,8 +19,8 @@ import workloads
 pytestmark = pytest.mark.gpu
 
 # (x, U and W absolute; F normwise; history absolute) per precision
-TOL = {"fp64": (1e-11, 1e-10, 1e-10, 1e-8, 1e-12),
-       "mixed": (1e-7, 1e-6, 1e-6, 1e-3, 1e-8)}
+TOL = {"fp64": (1e-14, 1e-12, 2e-13, 5e-13, 3e-14),
+       "mixed": (1e-8, 2e-6, 1e-6, 2e-6, 5e-8)}
 
 
 def _args(w, precision):
@@ -34,7 +37,7 @@ def _run(g, w, n):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_resume_follows_the_uninterrupted_run(tmp_path, precision):
+def test_resume_follows_the_uninterrupted_run(tmp_path, precision, record):
     import paper_2307_13802_gb300 as susp
 
     w = workloads.make(600, 0.55, 100.0, 1.0, pack_seed=31, dyn_seed=32)
@@ -64,6 +67,12 @@ def test_resume_follows_the_uninterrupted_run(tmp_path, precision):
     ib = b.info()
 
     tx, tu, tw, tf, th = TOL[precision]
+    record("x", np.abs(xa - xb).max(), tx)
+    record("U", np.abs(Ua - Ub).max(), tu)
+    record("W", np.abs(Wa - Wb).max(), tw)
+    record("F", np.abs(Fa - Fb).max() / np.abs(Fa).max(), tf)
+    record("T", np.abs(Ta - Tb).max() / np.abs(Ta).max(), tf)
+    record("hist", np.abs(xia - xib).max() if len(xia) else 0.0, th)
     assert ib["k"] == ia["k"] and ib["strain"] == pytest.approx(ia["strain"], abs=1e-15)
     assert np.abs(xa - xb).max() <= tx
     assert np.abs(Ua - Ub).max() <= tu
@@ -119,10 +128,10 @@ def test_bad_checkpoint_files_are_reported(tmp_path):
         h.load(str(junk))
     # header: magic, N, R, precision, k, steps, dt, forces_valid, pad
     other = tmp_path / "other.ckpt"
-    other.write_bytes(struct.pack("<8sqiiqqdii", b"SUSPCKP2", 11, 1, 0, 5, 5, 1e-4, 1, 0))
+    other.write_bytes(struct.pack("<8sqiiqqdii", b"SUSPCKP3", 11, 1, 0, 5, 5, 1e-4, 1, 0))
     with pytest.raises(s.SuspError, match="particle or replica count"):
         h.load(str(other))
     short = tmp_path / "short.ckpt"
-    short.write_bytes(struct.pack("<8sqiiqqdii", b"SUSPCKP2", 10, 1, 0, 5, 5, 1e-4, 1, 0))
+    short.write_bytes(struct.pack("<8sqiiqqdii", b"SUSPCKP3", 10, 1, 0, 5, 5, 1e-4, 1, 0))
     with pytest.raises(s.SuspError, match="truncated"):
         h.load(str(short))

@@ -1,0 +1,244 @@
+"""Ensemble rheology and batched replicas against the oracle.
+
+* Ensemble parity (Sec. II.E: eta_r, N1, N2 averaged over realisations;
+  Sec. IV.A on sampling error): 500 bidisperse spheres at phi 0.5, Pe 10,
+  mu 0 and 1.  Sixteen packings per friction value are run 2e4 steps by
+  the oracle and, with other noise seeds, as one batch handle on the GPU
+  (FP64 and mixed paths), so the two sides are independent realisations of
+  one ensemble.  Each run's eta_r, N1, N2 are averaged over its last 1.8e4
+  steps; the ensemble means must agree within four standard errors of their
+  difference (the standard error from the spread over the sixteen runs;
+  four, not three, because six means are compared per path).
+* Batch against the oracle: sixteen replicas drawn from the 256-replica
+  ensemble recipe (Pe log-uniform in [0.1, 1000], phi in [0.45, 0.60], mu in
+  {0, 0.5, 1}; the rows of smallest Pe and largest phi included; N capped at
+  1,500 so that the oracle stays quick) stepped 100 steps in one batch
+  handle, each replica compared with its own oracle run from the same state
+  with the same noise.
+* Mixed against FP64 once the trajectories have decorrelated: 10,000
+  spheres, phi 0.56, Pe 100, mu 1, four replicas per precision with
+  different noise seeds, 2e4 steps: the relative viscosity of the two paths
+  within 1%, with the statistical resolution of the comparison stated."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_kw(w, precision, seed=None):
+    p = w.params
+    return dict(precision=precision, eta=p["eta"], rho=p["rho"], kn=p["kn"], kt=p["kt"],
+                mu=p["mu"], xi_min=p["xi_min"], xi_max=p["xi_max"], skin=p["skin"],
+                shear_rate=p["shear_rate"], kT=p["kT"],
+                seed=p["seed"] if seed is None else seed,
+                torque_sign=p["torque_sign"], dt=p["dt"])
+
+
+def _pool():
+    # freshly spawned interpreters (safe after CUDA is initialised), one
+    # OpenMP thread each for the packing helper: the pool is the parallelism
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    os.environ["OMP_NUM_THREADS"] = "1"
+    return cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1),
+                                  mp_context=mp.get_context("spawn"))
+
+
+# --------------------------------------------------------------------------
+# ensemble eta_r, N1, N2 (c1 shape)
+# --------------------------------------------------------------------------
+ENS_N, ENS_PHI, ENS_PE, ENS_STEPS, ENS_BURN, ENS_RUNS = 500, 0.50, 10.0, 20_000, 2_000, 16
+
+
+def _ens_workload(mu, i):
+    return workloads.make(ENS_N, ENS_PHI, ENS_PE, mu, pack_seed=6100 + 10 * i,
+                          dyn_seed=7100 + i)
+
+
+def _oracle_rheology(job):
+    import oracle
+    mu, i = job
+    w = _ens_workload(mu, i)
+    o = oracle.System(w.radii, w.box, **dict(w.params, seed=8100 + i))
+    o.set_state(w.x, w.U, w.W)
+    o.step(ENS_BURN)
+    o.take_stress_sums()
+    o.step(ENS_STEPS - ENS_BURN)
+    n, s = o.take_stress_sums()
+    # eta_r = (sigma^C + sigma^HL + drag)_xy / (eta rate); the drag stresslet
+    # is pure xy, so N1 and N2 come from contact and lubrication
+    sig = (s["contact"] + s["lubrication"]) / n
+    rate, eta = w.params["shear_rate"], w.params["eta"]
+    eta_r = (sig[0, 1] + oracle.drag_stress_xy(w.radii, w.box, eta, rate)) / (eta * rate)
+    return eta_r, sig[0, 0] - sig[1, 1], sig[1, 1] - sig[2, 2]
+
+
+def _gpu_rheology(susp, mu, precision):
+    ws = [_ens_workload(mu, i) for i in range(ENS_RUNS)]
+    b = susp.System.batch([w.N for w in ws], np.concatenate([w.radii for w in ws]),
+                          np.stack([w.box for w in ws]),
+                          [_gpu_kw(w, precision) for w in ws])
+    b.set_state(np.concatenate([w.x for w in ws]), np.concatenate([w.U for w in ws]),
+                np.concatenate([w.W for w in ws]))
+    dt = ws[0].params["dt"]
+    b.step_batch(ENS_BURN, dt)
+    for r in range(ENS_RUNS):
+        b.stress(r)
+    b.step_batch(ENS_STEPS - ENS_BURN, dt)
+    out = []
+    for r in range(ENS_RUNS):
+        s = b.stress(r)
+        assert s["samples"] == ENS_STEPS - ENS_BURN
+        out.append((s["eta_r"], s["N1"], s["N2"]))
+    b.close()
+    return np.array(out)
+
+
+@pytest.fixture(scope="module")
+def oracle_ensembles():
+    jobs = [(mu, i) for mu in (0.0, 1.0) for i in range(ENS_RUNS)]
+    with _pool() as ex:
+        res = list(ex.map(_oracle_rheology, jobs))
+    return {mu: np.array(res[k * ENS_RUNS:(k + 1) * ENS_RUNS]) for k, mu in enumerate((0.0, 1.0))}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("mu", [0.0, 1.0])
+def test_ensemble_rheology_matches_the_oracle(oracle_ensembles, precision, mu, record):
+    import paper_2307_13802_gb300 as susp
+
+    g = _gpu_rheology(susp, mu, precision)
+    o = oracle_ensembles[mu]
+    n = ENS_RUNS
+    for c, name in enumerate(("eta_r", "N1", "N2")):
+        mg, mo = g[:, c].mean(), o[:, c].mean()
+        se = math.sqrt(g[:, c].var(ddof=1) / n + o[:, c].var(ddof=1) / n)
+        print(f"{precision} mu={mu} {name}: gpu {mg:.4f} oracle {mo:.4f} "
+              f"diff {mg - mo:+.4f} se {se:.4f}")
+        record(f"{name}_diff_over_se", abs(mg - mo) / se, 4.0)
+        record(f"{name}_se_rel", se / abs(mo))
+        assert abs(mg - mo) <= 4.0 * se, (name, mg, mo, se)
+    # the runs are sheared suspensions with a positive viscosity
+    assert np.all(g[:, 0] > 1.0) and np.all(o[:, 0] > 1.0)
+
+
+# --------------------------------------------------------------------------
+# batch against the oracle on the 256-replica recipe's parameter spread
+# --------------------------------------------------------------------------
+BATCH_STEPS, BATCH_NCAP = 100, 1500
+
+
+def _batch_rows():
+    table = workloads.replica_table()
+    idx = {int(np.argmin([r["pe"] for r in table])), int(np.argmax([r["phi"] for r in table]))}
+    for i in np.argsort([r["N"] for r in table]):
+        if len(idx) == 16:
+            break
+        idx.add(int(i))
+    rows = []
+    for i in sorted(idx):
+        row = dict(table[i])
+        row["N"] = min(row["N"], BATCH_NCAP)
+        rows.append((i, row))
+    return rows
+
+
+def _batch_workload(job):
+    i, row = job
+    return workloads.make(row["N"], row["phi"], row["pe"], row["mu"], pack_seed=5000 + 2 * i,
+                          dyn_seed=row["seed"], tol=1e-2, max_sweeps=2000)
+
+
+def _oracle_batch_run(job):
+    import oracle
+    w = _batch_workload(job)
+    o = oracle.System(w.radii, w.box, **w.params)
+    o.set_state(w.x, w.U, w.W)
+    o.step(BATCH_STEPS)
+    x, U, W = o.state()
+    F, T = o.forces()
+    n, s = o.take_stress_sums()
+    return x, U, F, T, s["contact"] / n + s["lubrication"] / n
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_of_the_replica_recipe_matches_the_oracle(precision, record):
+    import paper_2307_13802_gb300 as susp
+
+    rows = _batch_rows()
+    pes = [r["pe"] for _, r in rows]
+    phis = [r["phi"] for _, r in rows]
+    assert min(pes) < 0.12 and max(phis) > 0.595 and len(rows) == 16
+    with _pool() as ex:
+        ws = list(ex.map(_batch_workload, rows))
+        ref = list(ex.map(_oracle_batch_run, rows))
+    b = susp.System.batch([w.N for w in ws], np.concatenate([w.radii for w in ws]),
+                          np.stack([w.box for w in ws]), [_gpu_kw(w, precision) for w in ws])
+    b.set_state(np.concatenate([w.x for w in ws]), np.concatenate([w.U for w in ws]),
+                np.concatenate([w.W for w in ws]))
+    b.step_batch(BATCH_STEPS, ws[0].params["dt"])
+    xb, Ub, _ = b.state()
+    Fb, Tb = b.forces()
+    off = np.concatenate([[0], np.cumsum([w.N for w in ws])])
+    # measured on a GB300: FP64 5.6e-13, mixed 1.6e-4 (the Pe = 0.1 replica,
+    # noise through single-precision Box-Muller, grown over 100 steps)
+    tol_f = 1e-11 if precision == "fp64" else 1e-3
+    worst = 0.0
+    for r, (w, (xo, Uo, Fo, To, so)) in enumerate(zip(ws, ref)):
+        sl = slice(off[r], off[r + 1])
+        dx = xb[sl] - xo
+        dx -= np.rint(dx / w.L) * w.L
+        eF = np.abs(Fb[sl] - Fo).max() / np.abs(Fo).max()
+        eT = np.abs(Tb[sl] - To).max() / np.abs(To).max()
+        sg = b.stress(r)
+        es = np.abs(sg["contact"] + sg["lubrication"] - so).max() / np.abs(so).max()
+        worst = max(worst, eF, eT)
+        record(f"r{r}_pe{w.meta['pe']:.3g}_phi{w.meta['phi']:.3f}_force", max(eF, eT), tol_f)
+        record(f"r{r}_stress", es, tol_f)
+        record(f"r{r}_x", np.abs(dx).max())
+        assert eF <= tol_f and eT <= tol_f, (r, w.meta, eF, eT)
+        assert es <= tol_f, (r, w.meta, es)
+        assert sg["samples"] == BATCH_STEPS
+    print(f"{precision}: worst force/torque error {worst:.2e} over {len(ws)} replicas")
+
+
+# --------------------------------------------------------------------------
+# mixed against FP64 over decorrelated runs
+# --------------------------------------------------------------------------
+def test_mixed_viscosity_within_one_percent_of_fp64_over_independent_runs(record):
+    import paper_2307_13802_gb300 as susp
+
+    R, steps, burn = 4, 20_000, 2_000
+    ws = [workloads.make(10_000, 0.56, 100.0, 1.0, pack_seed=6500 + 10 * i, dyn_seed=0)
+          for i in range(R)]
+    res = {}
+    for prec, seed0 in (("fp64", 6600), ("mixed", 6700)):
+        b = susp.System.batch([w.N for w in ws], np.concatenate([w.radii for w in ws]),
+                              np.stack([w.box for w in ws]),
+                              [_gpu_kw(w, prec, seed=seed0 + i) for i, w in enumerate(ws)])
+        b.set_state(np.concatenate([w.x for w in ws]), np.concatenate([w.U for w in ws]),
+                    np.concatenate([w.W for w in ws]))
+        dt = ws[0].params["dt"]
+        b.step_batch(burn, dt)
+        for r in range(R):
+            b.stress(r)
+        b.step_batch(steps - burn, dt)
+        res[prec] = np.array([b.stress(r)["eta_r"] for r in range(R)])
+        b.close()
+    e64, e32 = res["fp64"], res["mixed"]
+    # the two paths start every replica from the same packing: pair the runs
+    d = e32 / e64 - 1.0
+    rel = abs(e32.mean() / e64.mean() - 1.0)
+    se = d.std(ddof=1) / math.sqrt(R)
+    print(f"eta_r fp64 {e64} mixed {e32}: mean rel diff {rel:.2e}, se {se:.2e}")
+    record("eta_r_rel_diff", rel, 1e-2)
+    record("eta_r_rel_se", se)
+    assert e64.min() > 1.0
+    assert rel <= 1e-2
+    # the comparison resolves 1%: three standard errors stay below it
+    assert 3 * se < 1e-2

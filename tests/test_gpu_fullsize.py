@@ -9,12 +9,15 @@ by brute force in numpy with the sliding-brick minimum image) and its global
 tags for the noise counters, the oracle's evaluation of that cluster gives
 the exact FP64 force and torque on the sampled sphere.
 
-Bars: the FP64 path 1e-11 of the largest sampled entry (as at small sizes);
-the mixed path 2e-5 with the noise off and 3e-3 with it on (the same Philox
-words through 24-bit uniforms and fast log/sin/cos change the noise at the
-1e-3 level, as the bench's mixed-vs-FP64 line reports).  A property that
-holds at any size is checked on the whole system: with the one-body terms
-and noise off, the pair forces cancel (Newton's third law)."""
+Bars: the FP64 path 1e-11 of the largest sampled entry (the required
+agreement; measured <= 4.8e-16); the mixed path 1e-5 with the noise off
+(measured <= 6.8e-7 at 1M and 1.1e-6 at 8M) and 2e-5 with it on (measured
+1.3e-6: the same Philox words through 24-bit uniforms and the fast
+log/sin/cos move single deviates by ~1e-6 relative), each 10-20 times the
+largest error measured on a GB300.  A property that holds at any size is
+checked on the whole system: with the one-body terms and noise off, the pair
+forces cancel (Newton's third law; measured 9e-17 FP64 and 2.7e-10 mixed of
+the summed magnitudes, bars 1e-14 and 5e-9)."""
 import numpy as np
 import pytest
 
@@ -83,7 +86,7 @@ def _oracle_on_sample(w, x, U, W, sample, **kw):
     return F, T, np.mean(sizes)
 
 
-def _check(susp, w, precision, nsample, tol, **kw):
+def _check(susp, w, precision, nsample, tol, record=None, **kw):
     g = _gpu(susp, w, precision, **kw)
     F, T = g.forces()
     x, U, W = g.state()                  # the wrapped state the library evaluated
@@ -94,27 +97,31 @@ def _check(susp, w, precision, nsample, tol, **kw):
     eF = np.abs(F[sample] - Fo).max() / np.abs(Fo).max()
     eT = np.abs(T[sample] - To).max() / np.abs(To).max()
     print(f"{precision} N={w.N}: force {eF:.2e}, torque {eT:.2e} over {nsample} spheres")
+    if record is not None:
+        record(f"{precision}_N{w.N}_force", eF, tol)
+        record(f"{precision}_N{w.N}_torque", eT, tol)
     assert eF <= tol and eT <= tol
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 3e-3)])
-def test_bench_workload_sampled_against_the_oracle(susp, w1m, precision, tol):
-    _check(susp, w1m, precision, 128, tol)
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 2e-5)])
+def test_bench_workload_sampled_against_the_oracle(susp, w1m, precision, tol, record):
+    _check(susp, w1m, precision, 128, tol, record)
 
 
-def test_bench_workload_mixed_without_noise(susp, w1m):
-    _check(susp, w1m, "mixed", 128, 2e-5, noise=0)
+def test_bench_workload_mixed_without_noise(susp, w1m, record):
+    _check(susp, w1m, "mixed", 128, 1e-5, record, noise=0)
 
 
-def test_largest_workload_sampled_against_the_oracle(susp, w8m):
-    _check(susp, w8m, "fp64", 48, 1e-11)
-    _check(susp, w8m, "mixed", 48, 2e-5, noise=0)
+def test_largest_workload_sampled_against_the_oracle(susp, w8m, record):
+    _check(susp, w8m, "fp64", 48, 1e-11, record)
+    _check(susp, w8m, "mixed", 48, 2e-5, record, noise=0)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-6)])
-def test_pair_forces_cancel_over_the_whole_bench_system(susp, w1m, precision, tol):
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-14), ("mixed", 5e-9)])
+def test_pair_forces_cancel_over_the_whole_bench_system(susp, w1m, precision, tol, record):
     g = _gpu(susp, w1m, precision, onebody=0, noise=0)
     F, _ = g.forces()
+    record("net_force", np.abs(F.sum(axis=0)).max() / np.abs(F).sum(axis=0).max(), tol)
     assert np.abs(F.sum(axis=0)).max() <= tol * np.abs(F).sum(axis=0).max()
 
 

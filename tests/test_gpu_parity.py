@@ -5,10 +5,17 @@ Tolerances: the FP64 path evaluates the oracle's expressions with no
 multiply-add contraction, except that the resistances and the unit vector
 take reciprocal products in place of the printed quotients (a few ulps);
 beyond that they differ only in the last bits of log, sin, cos (CUDA vs libm)
-and in the order of the force sums (atomics).  So forces,
-torques and stresses of one evaluation agree to 1e-11 relative to the
-largest entry of the same quantity (normwise), and neighbour sets, which are
-decided by the same d^2 < r_list^2 expression, agree exactly."""
+and in the order of the force sums (atomics).  The required agreement of
+one evaluation is 1e-11 relative to the largest entry of the same quantity
+(normwise); measured, forces, torques and stresses agree to <= 3.2e-15, and
+the bar is set at 1e-13, about 30 times that.  Neighbour sets, which are
+decided by the same d^2 < r_list^2 expression, agree exactly.
+
+Bars of the longer runs are 10-25 times the largest error measured on a
+GB300 (the atomics change the summation order from run to run, and the
+trajectories amplify rounding): after 1,000 steps forces agree to 1.4e-12
+(bar 2e-11) and the time-averaged stresses to 7.9e-13 (bar 1e-11); the
+tangential history after 300 frictional steps to 2.0e-13 (bar 3e-12)."""
 import numpy as np
 import pytest
 
@@ -17,7 +24,7 @@ import workloads
 
 pytestmark = pytest.mark.gpu
 
-RTOL_FP64 = 1e-11
+RTOL_FP64 = 1e-13
 
 
 @pytest.fixture(scope="module")
@@ -51,7 +58,7 @@ CASES = [
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"N{c['N']}-phi{c['phi']}-pe{c['pe']}-mu{c['mu']}")
 @pytest.mark.parametrize("strain", [0.0, 0.37, -0.49])
-def test_one_evaluation_matches_oracle(susp, case, strain):
+def test_one_evaluation_matches_oracle(susp, case, strain, record):
     w = workloads.make(case["N"], case["phi"], case["pe"], case["mu"], poly=case["poly"],
                        pack_seed=11, dyn_seed=12)
     # compress a little so that many pairs overlap
@@ -72,6 +79,10 @@ def test_one_evaluation_matches_oracle(susp, case, strain):
     Fo, To = o.forces()
     so = o.stress()
     assert o.info()["ncontacts"] > 10
+    record("force", _relerr(F, Fo), RTOL_FP64)
+    record("torque", _relerr(T, To), RTOL_FP64)
+    for key in ("contact", "lubrication", "brownian"):
+        record(key, _relerr(sg[key], so[key]), RTOL_FP64)
     assert _relerr(F, Fo) <= RTOL_FP64
     assert _relerr(T, To) <= RTOL_FP64
     for key in ("contact", "lubrication", "brownian"):
@@ -117,7 +128,7 @@ def test_neighbour_list_after_shearing_is_brute_force(susp):
 
 @pytest.mark.parametrize("graphs", [0, 1])
 @pytest.mark.parametrize("mu", [0.0, 1.0])
-def test_trajectory_parity_500_spheres(susp, graphs, mu):
+def test_trajectory_parity_500_spheres(susp, graphs, mu, record):
     # 500 bidisperse spheres, phi = 0.5, Pe = 10: 1000 steps of 1e-4 on both
     w = workloads.make(500, 0.50, 10.0, mu, pack_seed=1001, dyn_seed=2001)
     p = w.params
@@ -126,6 +137,7 @@ def test_trajectory_parity_500_spheres(susp, graphs, mu):
     o = oracle.System(w.radii, w.box, **p)
     o.set_state(w.x, w.U, w.W)
     errs = []
+    serr = 0.0
     for chunk in range(10):
         g.step(100, p["shear_rate"], p["kT"], p["dt"], p["seed"])
         o.step(100)
@@ -136,15 +148,19 @@ def test_trajectory_parity_500_spheres(susp, graphs, mu):
         sg = g.stress()
         assert sg["samples"] == n == 100
         for key in ("contact", "lubrication", "brownian"):
-            assert _relerr(sg[key], so[key] / n) <= 1e-7, (chunk, key)
+            serr = max(serr, _relerr(sg[key], so[key] / n))
+            assert _relerr(sg[key], so[key] / n) <= 1e-11, (chunk, key)
     print("per-chunk max relative force error:", ["%.1e" % e for e in errs])
-    assert errs[0] <= 1e-9
-    assert max(errs) <= 1e-6
+    record("first_chunk_force", errs[0], 1e-12)
+    record("max_chunk_force", max(errs), 2e-11)
+    record("stress_avg", serr, 1e-11)
+    assert errs[0] <= 1e-12
+    assert max(errs) <= 2e-11
     if graphs:
         assert g.info()["graph_steps"] > 0
 
 
-def test_friction_history_parity(susp):
+def test_friction_history_parity(susp, record):
     w = workloads.make(600, 0.55, 100.0, 1.0, pack_seed=41, dyn_seed=42)
     p = w.params
     g = _gpu_system(susp, w)
@@ -158,10 +174,13 @@ def test_friction_history_parity(susp):
     sel = ocontact.astype(bool)
     assert len(ij) == sel.sum() > 20
     assert np.array_equal(ij, oij[sel])
-    assert _relerr(xi, ohist[sel]) <= 1e-7
     F, T = g.forces()
     Fo, To = o.forces()
-    assert _relerr(F, Fo) <= 1e-7 and _relerr(T, To) <= 1e-7
+    record("history", _relerr(xi, ohist[sel]), 3e-12)
+    record("force", _relerr(F, Fo), 3e-12)
+    record("torque", _relerr(T, To), 3e-12)
+    assert _relerr(xi, ohist[sel]) <= 3e-12
+    assert _relerr(F, Fo) <= 3e-12 and _relerr(T, To) <= 3e-12
 
 
 def test_errors_are_reported(susp):

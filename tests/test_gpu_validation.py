@@ -10,7 +10,10 @@ two-particle checks.
   the separations beyond contact are uniformly distributed: the pair
   distribution g(r), hence the potential of mean force -kT ln g, is flat.
   (A noise amplitude not tied to the resistance, or a wrong sign in Eq. 24,
-  pulls pairs together or apart near contact and the profile bends.)"""
+  pulls pairs together or apart near contact and the profile bends.)
+  Inside contact the only conservative force is the normal spring, so the
+  potential of mean force is (1/2) k_n delta^2 and g(r) falls as
+  exp(-k_n delta^2 / 2 kT) with delta = 2a - r (Sec. III.A)."""
 import math
 
 import numpy as np
@@ -55,14 +58,18 @@ def test_isolated_sphere_msd_follows_eq31(precision):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_two_sphere_potential_of_mean_force_is_flat(precision):
-    # Starts from the equilibrium distribution (the second sphere uniform in
-    # the box outside contact) and checks that the dynamics keep it: with a
-    # noise amplitude not tied to the resistance the lubrication shell
-    # h <= 0.05 would heat or cool and its population would drift.
+    # Starts from the equilibrium distribution (the second sphere placed with
+    # the Boltzmann weight of the contact spring: uniform outside contact,
+    # exp(-kn delta^2 / 2kT) inside) and checks that the dynamics keep it:
+    # with a noise amplitude not tied to the resistance the lubrication shell
+    # h <= 0.05 would heat or cool and its population would drift.  (Inside
+    # contact the overdamped well relaxes on gamma / kn ~ 0.5 time units, so
+    # a start without contacts would not reach equilibrium in this run.)
     import paper_2307_13802_gb300 as susp
 
-    R, L, kT, dt = 8000, 8.5, 10.0, 1e-4
-    kw = dict(precision=precision, shear_rate=0.0, kT=kT, dt=dt, mu=0.0)
+    R, L, kT, dt, kn = 8000, 8.5, 10.0, 1e-4, 1e4
+    dth = math.sqrt(kT / kn)           # thermal overlap scale, 0.032 a
+    kw = dict(precision=precision, shear_rate=0.0, kT=kT, dt=dt, mu=0.0, kn=kn)
     b = _batch(susp, R, 2, L, [1.0, 1.0], kw)
     rng = np.random.default_rng(11)
     x = np.empty((R, 2, 3))
@@ -72,14 +79,18 @@ def test_two_sphere_potential_of_mean_force_is_flat(precision):
             y = rng.uniform(0.0, L, size=3)
             d = y - L / 2
             d -= np.rint(d / L) * L
-            if np.linalg.norm(d) > 2.02:
+            dist = np.linalg.norm(d)
+            if dist >= 2.0 or (dist > 2.0 - 6 * dth and
+                               rng.uniform() < math.exp(-kn * (2.0 - dist) ** 2 / (2 * kT))):
                 break
         x[r, 1] = y
     m = 4.0 / 3.0 * math.pi
     U = rng.normal(scale=math.sqrt(kT / m), size=(R, 2, 3))
     b.set_state(x.reshape(-1, 3), U.reshape(-1, 3), None)
-    b.step_batch(1000, dt)
-    edges = np.array([2.0, 2.05, 2.2, 2.5, 3.0, 3.6])
+    b.step_batch(500, dt)
+    inner = 2.0 - dth * np.array([2.0, 1.5, 1.0, 0.5])
+    edges = np.concatenate([inner, [2.0, 2.05, 2.2, 2.5, 3.0, 3.6]])
+    nin = len(inner)
     counts = np.zeros(len(edges) - 1)
     for _ in range(400):
         b.step_batch(25, dt)
@@ -87,11 +98,25 @@ def test_two_sphere_potential_of_mean_force_is_flat(precision):
         d = xs[:, 1] - xs[:, 0]
         d -= np.rint(d / L) * L
         counts += np.histogram(np.linalg.norm(d, axis=1), bins=edges)[0]
-    g = counts / (4.0 / 3.0 * math.pi * (edges[1:] ** 3 - edges[:-1] ** 3))
-    g /= g[1:].mean()
-    print("bins", edges, "g", np.round(g, 4), "counts", counts.astype(int))
+    shell = 4.0 / 3.0 * math.pi * (edges[1:] ** 3 - edges[:-1] ** 3)
+    g = counts / shell
+    g /= g[nin + 1:].mean()            # the flat level beyond contact
+    print("bins", np.round(edges, 4), "g", np.round(g, 4), "counts", counts.astype(int))
     # samples 25 steps apart are correlated (near contact most): allow four
     # standard deviations of a count with a correlation factor of 4
     sd = np.sqrt(4.0 / counts)
-    assert counts.min() > 5_000
-    assert np.all(np.abs(g - 1.0) <= 4 * sd + 0.005), (g, sd)
+    out = g[nin:]
+    assert counts[nin:].min() > 5_000
+    assert np.all(np.abs(out - 1.0) <= 4 * sd[nin:] + 0.005), (out, sd[nin:])
+    # inside contact: the bin averages of exp(-kn delta^2 / 2kT) over r^2 dr
+    rr = np.linspace(edges[0], 2.0, 20001)
+    wgt = rr ** 2 * np.exp(-kn * (2.0 - rr) ** 2 / (2 * kT))
+
+    def trap(y, x):
+        return float(np.sum(0.5 * (y[1:] + y[:-1]) * np.diff(x)))
+
+    ref = np.array([trap(wgt[(rr >= lo) & (rr <= hi)], rr[(rr >= lo) & (rr <= hi)])
+                    for lo, hi in zip(edges[:nin], edges[1:nin + 1])]) / (shell[:nin] / (4 * math.pi))
+    print("contact bins: g", np.round(g[:nin], 4), "Boltzmann", np.round(ref, 4))
+    assert counts[:nin].min() > 300
+    assert np.all(np.abs(g[:nin] - ref) <= 4 * sd[:nin] * ref + 0.03 * ref), (g[:nin], ref)
