@@ -309,6 +309,16 @@ int susp_get_series(susp_t* h, int32_t replica, double* out, int64_t cap,
 int susp_green_kubo(const double* x, int64_t n, int64_t max_lag, double dt,
                     double V, double kT, double* C, double* eta, double* fit);
 
+/* ---- diagnostics ------------------------------------------------------------- */
+/* Measured peak multiply-add rates of the current device, the denominators
+ * of the arithmetic rooflines: out[0] FP64 and out[1] FP32 GFLOP/s (two
+ * operations per fused multiply-add), from a kernel of eight independent
+ * multiply-add chains per thread on 8 blocks of 256 threads per SM, the best
+ * of three launches timed with CUDA events on the legacy default stream.
+ * Errors: SUSP_EINVAL (NULL), SUSP_ENODEV, SUSP_ENOMEM, SUSP_ECUDA; message
+ * in susp_create_error(). */
+int susp_measure_peaks(double* out);
+
 /* ---- without allocation ------------------------------------------------------ */
 /* The paper has no counterpart to this call; it is a service for callers
  * that cannot allocate device memory where they need the answer (code
@@ -334,8 +344,10 @@ int susp_green_kubo(const double* x, int64_t n, int64_t max_lag, double dt,
  * The call allocates nothing: its scratch is a fixed array in device memory
  * that every GPU which loads the library holds until the process exits.
  * npairs above SUSP_NOALLOC_MAX_PAIRS is rejected with SUSP_EINVAL.  The
- * first call on each device looks up that array's device address (with the
- * device current), so make the first call before any stream capture.  All
+ * first call in each CUDA context (the device's primary context unless the
+ * caller made another one current) looks up that array's device address in
+ * that context, so make the first call before any stream capture; a device
+ * reset or another context gets a fresh look-up.  All
  * calls share the array: calls whose work overlaps on the GPU (several
  * streams, or several host threads) race and give wrong results; calls on
  * one stream are ordered and safe.  Errors: SUSP_EINVAL (NULL pointer,

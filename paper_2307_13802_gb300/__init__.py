@@ -90,6 +90,7 @@ _SIGNATURES = {
                                            C.c_double, C.POINTER(susp_params), C.c_double,
                                            C.c_int64, C.c_void_p, C.c_void_p]),
     "susp_get_series": (C.c_int, [_H, C.c_int32, _D, C.c_int64, _I64, _I64]),
+    "susp_measure_peaks": (C.c_int, [_D]),
     "susp_green_kubo": (C.c_int, [_D, C.c_int64, C.c_int64, C.c_double, C.c_double,
                                   C.c_double, _D, _D, _D]),
     "susp_set_skin": (C.c_int, [_H, C.c_double]),
@@ -170,6 +171,13 @@ def torch_allocator(device=None):
         torch.cuda.caching_allocator_delete(int(ptr))
 
     return alloc, release
+
+
+def measure_peaks() -> dict:
+    """Peak FP64 and FP32 multiply-add rates of the current device (GFLOP/s)."""
+    out = np.zeros(2)
+    check(lib.susp_measure_peaks(_dp(out)))
+    return {"fp64_gflops": float(out[0]), "fp32_gflops": float(out[1])}
 
 
 def check(code: int, h=None):

@@ -1509,6 +1509,52 @@ int susp_get_series(susp_t* h, int32_t replica, double* out, int64_t cap, int64_
   return SUSP_OK;
 }
 
+int susp_measure_peaks(double* out) {
+  g_create_error.clear();
+  if (!out) { g_create_error = "out is NULL"; return SUSP_EINVAL; }
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    g_create_error = "no CUDA device";
+    return SUSP_ENODEV;
+  }
+  void* sink = nullptr;
+  if (cudaMalloc(&sink, 256 * sizeof(double)) != cudaSuccess) {
+    g_create_error = "cudaMalloc failed";
+    return SUSP_ENOMEM;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int blocks = nsm * 8;
+  for (int t = 0; t < 2; ++t) {
+    const int fp64 = t == 0;
+    const int iters = fp64 ? 4096 : 65536;
+    launch_fma_peak(fp64, sink, blocks, iters / 8, nullptr);  // warm-up
+    float best = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, nullptr);
+      launch_fma_peak(fp64, sink, blocks, iters, nullptr);
+      cudaEventRecord(e1, nullptr);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep == 0 || ms < best) best = ms;
+    }
+    // two floating-point operations per multiply-add
+    out[t] = 2.0 * 8.0 * (double)iters * 256.0 * (double)blocks / (best * 1e-3) / 1e9;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    g_create_error = std::string("peak kernels failed: ") + cudaGetErrorString(e);
+    return SUSP_ECUDA;
+  }
+  return SUSP_OK;
+}
+
 int susp_green_kubo(const double* x, int64_t n, int64_t max_lag, double dt, double V,
                     double kT, double* C, double* eta, double* fit) {
   g_create_error.clear();

@@ -42,17 +42,21 @@ __device__ __forceinline__ bool wrap_le(double& x, double& y, double& z,
   return guard < 64;
 }
 
-// Last-block bookkeeping shared by the FP64 and mixed integrators.
+// Last-block bookkeeping, run by every thread of the block that finishes
+// last: the threads advance the replicas' strains in parallel (thread t takes
+// replicas t, t + blockDim, ...), then thread 0 does the global part.
 __device__ void integrator_epilogue(const Arrays& A, const StepArgs& s,
                                     unsigned long long cond_handle,
                                     int use_cond) {
   Ctl* ctl = A.ctl;
-  for (int r = 0; r < A.R; ++r) {
+  for (int r = threadIdx.x; r < A.R; r += blockDim.x) {
     Replica& R = A.repl[r];
     const double st = next_strain(R);
     R.strain = st;
     R.tilt = st * R.L[1];
   }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   ctl->k = ctl->k + 1;
   const double vmax = __longlong_as_double((long long)ctl->vmax_bits);
   ctl->vmax_bits = 0ull;
@@ -141,7 +145,7 @@ k_integrate_fp64(Arrays A, BlockMap bm, StepArgs s, int close, int sample_kin,
     last = (t == (unsigned int)gridDim.x - 1u);
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
+  if (last) {
     __threadfence();
     integrator_epilogue(A, s, cond_handle, use_cond);
   }

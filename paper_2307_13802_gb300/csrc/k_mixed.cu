@@ -104,20 +104,26 @@ __device__ __forceinline__ void kick(DF3& v, float4 f, float c) {
 }
 
 // Last-block bookkeeping (strain, k, rebuild decision) as in the FP64 path,
-// plus the double-float fields the next step reads.
+// plus the double-float fields the next step reads.  Every thread of the
+// block that finishes last runs it: the replicas are advanced in parallel
+// (thread t takes replicas t, t + blockDim, ...), then thread 0 does the
+// global part.
 __device__ void epilogue_mixed(const Arrays& A, const StepArgs& s,
                                unsigned long long cond_handle, int use_cond) {
   Ctl* ctl = A.ctl;
-  for (int r = 0; r < A.R; ++r) {
+  for (int r = threadIdx.x; r < A.R; r += blockDim.x) {
     Replica& R = A.repl[r];
     const double st = advance_strain(R.strain, R.rate_dt, R.flip_at, R.flip_by);
     // a flip moves every home-cell origin by a fraction of Lx: the
-    // cell-relative mirrors need fresh home cells
+    // cell-relative mirrors need fresh home cells (every thread that sees
+    // one writes the same 1)
     if (st < R.strain && R.rate_dt > 0.0) ctl->need_rebuild = 1;
     R.strain = st;
     R.tilt = R.strain * R.L[1];
     refresh_strain_fields(R);
   }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   ctl->k = ctl->k + 1;
   const double vmax = (double)__uint_as_float(ctl->vmax_fbits);
   ctl->vmax_fbits = 0u;
@@ -240,16 +246,19 @@ k_integrate_mixed(Arrays A, BlockMap bm, StepArgs s, int close, int sample_kin,
     for (int w2 = 0; w2 < kBlock / 32; ++w2) sum += sk[w2 * kKinLen + threadIdx.x];
     A.kin_partial[(int64_t)b * kKinLen + threadIdx.x] = (double)sum;
   }
+  __shared__ int s_last;
   if (threadIdx.x == 0) {
     float bmax = 0.0f;
     for (int w2 = 0; w2 < kBlock / 32; ++w2) bmax = fmaxf(bmax, svmax[w2]);
     atomicMax(&ctl->vmax_fbits, __float_as_uint(bmax));
     __threadfence();
     const unsigned int tk = atomicAdd(&ctl->ticket, 1u);
-    if (tk == (unsigned int)gridDim.x - 1u) {
-      __threadfence();
-      epilogue_mixed(A, s, cond_handle, use_cond);
-    }
+    s_last = tk == (unsigned int)gridDim.x - 1u;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    epilogue_mixed(A, s, cond_handle, use_cond);
   }
 }
 

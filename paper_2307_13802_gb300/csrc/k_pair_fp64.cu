@@ -32,41 +32,6 @@
 
 namespace susp {
 
-// Scalar resistances of Eqs. 9-12 and 15-18 with the quotients of the
-// printed forms taken as products with four reciprocals (beta = a_j/a_i,
-// r = 1/(1 + beta), 1/beta, ixi = 1/xi_e); algebraically the same, and
-// within a few ulps of the printed forms (1/(1 + 1/beta) = beta r):
-//   XA11 = 6 pi eta a_i r^3 (2 beta^2 ixi + beta (1 + 7 beta + beta^2)/5 L)
-//   YA11 = 6 pi eta a_i r^3 (4 beta (2 + beta + 2 beta^2)/15) L
-//   YB11 = -4 pi eta a_i^2 r^2 (beta (4 + beta)/5) L
-//   YB21 = -4 pi eta a_j^2 r^2 ((4 beta + 1)/5) L
-//   YC11 = 8 pi eta a_i^3 r (2 beta/5) L,   YC12 = 8 pi eta a_i^3 r (beta^2/10) L
-//   YC22 = 8 pi eta a_j^3 r (2/5) L,        YC21 = 8 pi eta a_j^3 r (1/(10 beta)) L
-// with L = ln(1/xi_e).
-__device__ __forceinline__ Res8<double> resistances_rcp(double eta, double ai, double aj,
-                                                        double ixi, double L) {
-  const double pi = 3.14159265358979323846;
-  const double beta = aj / ai;
-  const double ibeta = ai / aj;
-  const double r = 1.0 / (1.0 + beta);
-  const double r2 = r * r, r3 = r2 * r;
-  const double b2 = beta * beta;
-  const double ta = 6.0 * pi * eta * ai * r3;
-  Res8<double> R;
-  R.XA11 = ta * (2.0 * b2 * ixi + 0.2 * beta * (1.0 + 7.0 * beta + b2) * L);
-  R.YA11 = ta * ((4.0 / 15.0) * beta * (2.0 + beta + 2.0 * b2) * L);
-  const double tb = -4.0 * pi * eta * r2 * 0.2 * L;
-  R.YB11 = tb * ai * ai * (beta * (4.0 + beta));
-  R.YB21 = tb * aj * aj * (4.0 * beta + 1.0);
-  const double tc = 8.0 * pi * eta * r * L;
-  const double ai3 = ai * ai * ai, aj3 = aj * aj * aj;
-  R.YC11 = tc * ai3 * (0.4 * beta);
-  R.YC12 = tc * ai3 * (0.1 * b2);
-  R.YC22 = tc * aj3 * 0.4;
-  R.YC21 = tc * aj3 * (0.1 * ibeta);
-  return R;
-}
-
 template <bool NOISE, bool FRIC, bool SAMPLE>
 __global__ void __launch_bounds__(kBlock)
 k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {

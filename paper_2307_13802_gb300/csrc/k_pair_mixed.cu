@@ -401,20 +401,27 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
     return o;
   };
 
-  // One batch of `count` (warp-uniform, 1..32) consecutive entries of queue
-  // qi.  Queue entries are in row order, so the owners along a batch are
-  // non-decreasing: the owner's shares are summed over each run of equal
-  // owners by shuffles, and the run's first lane adds the sums to the
-  // owner's shared-memory accumulators (one writer per owner per batch).
-  auto batch = [&](int qi, int first, int count) {
+  // One batch: lanes [0, n0) take entries first0.. of queue 0, lanes
+  // [n0, n0 + n1) entries first1.. of queue 1 (n0 + n1 <= 32, warp-uniform;
+  // a full batch comes from one queue, the last batch of a warp may hold
+  // both).  Queue entries are in row order, so the keys own + 32 * queue
+  // along a batch are non-decreasing: the owner's shares are summed over
+  // each run of equal keys by shuffles, and the run's first lane adds the
+  // sums to the owner's shared-memory accumulators -- the queue-0 runs
+  // first, then the queue-1 runs, so an owner with a run in each part has
+  // one writer at a time.
+  auto batch = [&](int n0, int first0, int n1, int first1) {
     float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     unsigned long long mb = 0ull;
-    int own = 32;  // idle lanes: past every owner
+    int own = 64;  // idle lanes: past every key
     float FR[3] = {0.f, 0.f, 0.f}, rro[3] = {0.f, 0.f, 0.f};
     float vp[32];
 #pragma unroll
     for (int cc = 0; cc < 32; ++cc) vp[cc] = 0.0f;
-    if (lane < count) own = physics(qi, first + lane, v, mb, FR, rro, vp);
+    const int qi = lane < n0 ? 0 : 1;
+    if (lane < n0 + n1)
+      own = physics(qi, qi ? first1 + lane - n0 : first0 + lane, v, mb, FR, rro, vp) +
+            32 * qi;
     if (SAMPLE) vacc += warp_reduce_scatter32(vp, lane);
     if (SAMPLE && rep_on) {
       // repulsion virial F^R (x) r summed over the warp into its slots
@@ -431,30 +438,35 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
       const int oo = __shfl_down_sync(kFull, own, off);
-      const bool same = lane + off < 32 && oo == own && own < 32;
+      const bool same = lane + off < 32 && oo == own && own < 64;
       if (!__any_sync(kFull, same)) break;  // every run is at most off long
 #pragma unroll
       for (int cc = 0; cc < 6; ++cc) {
         const float x = __shfl_down_sync(kFull, v[cc], off);
         if (same) v[cc] += x;
       }
-      if (FRIC && qi == 1) {
+      if (FRIC && n1 > 0) {
         const unsigned long long x = __shfl_down_sync(kFull, mb, off);
         if (same) mb |= x;
       }
     }
     const int prev = __shfl_up_sync(kFull, own, 1);
-    if (own < 32 && (lane == 0 || prev != own)) {
-      float4* so = &sF[warp * 32 + own];
-      float4* st = &sT[warp * 32 + own];
-      float4 f = *so, t = *st;
-      f.x += v[0]; f.y += v[1]; f.z += v[2];
-      t.x += v[3]; t.y += v[4]; t.z += v[5];
-      *so = f;
-      *st = t;
-      if (FRIC && qi == 1) sM[warp * 32 + own] |= mb;
+    const bool head = own < 64 && (lane == 0 || prev != own);
+#pragma unroll
+    for (int part = 0; part < 2; ++part) {
+      if (head && (own >> 5) == part) {
+        const int o = own & 31;
+        float4* so = &sF[warp * 32 + o];
+        float4* st = &sT[warp * 32 + o];
+        float4 f = *so, t = *st;
+        f.x += v[0]; f.y += v[1]; f.z += v[2];
+        t.x += v[3]; t.y += v[4]; t.z += v[5];
+        *so = f;
+        *st = t;
+        if (FRIC && part == 1) sM[warp * 32 + o] |= mb;
+      }
+      __syncwarp();
     }
-    __syncwarp();
   };
 
   // Work loop of the warp, all decisions warp-uniform: flush a queue that
@@ -479,11 +491,11 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   if (total > 0) locate(0);
   int base = 0;
   while (true) {
-    int qi = -1, first = 0, count = 0;
+    int n0 = 0, f0 = 0, n1 = 0, f1 = 0;
     if (qn0 >= 32) {
-      qi = 0; first = qn0 - 32; count = 32;
+      n0 = 32; f0 = qn0 - 32;
     } else if (qn1 >= 32) {
-      qi = 1; first = qn1 - 32; count = 32;
+      n1 = 32; f1 = qn1 - 32;
     } else if (base < total) {
       const int t = base + lane;
       const int o = o_n, sl = sl_n, q = q_n;
@@ -585,15 +597,18 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
       __syncwarp();
       base += 32;
       continue;
-    } else if (qn0 > 0) {
-      qi = 0; count = qn0;
-    } else if (qn1 > 0) {
-      qi = 1; count = qn1;
+    } else if (qn0 + qn1 > 32) {
+      // what is left does not fit one batch: the touching pairs first
+      n1 = qn1;
+    } else if (qn0 + qn1 > 0) {
+      // the warp's last batch: both queues' remainders together
+      n0 = qn0; n1 = qn1;
     } else {
       break;
     }
-    batch(qi, first, count);
-    if (qi == 0) qn0 -= count; else qn1 -= count;
+    batch(n0, f0, n1, f1);
+    qn0 -= n0;
+    qn1 -= n1;
   }
   // the warp's own accumulators are complete once its batches are done
   if (active) {

@@ -175,6 +175,33 @@ __global__ void k_autocorr(const double* __restrict__ x, int64_t n, int64_t max_
   }
 }
 
+// Peak multiply-add rate of the arithmetic type T: every thread runs eight
+// independent chains a = a * b + c (explicit fused multiply-adds), so the
+// pipe stays busy; the sums go to `sink` only if they equal a value they
+// cannot take, which keeps the work from being optimised away.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_peak(T* sink, int iters, T b, T c) {
+  T a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = (T)(threadIdx.x + k) * (T)1e-3;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+  }
+  T s = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += a[k];
+  if (s == (T)-12345.0) sink[threadIdx.x] = s;
+}
+
+// multiply-adds issued: blocks * 256 threads * iters * 8 chains
+void launch_fma_peak(int fp64, void* sink, int blocks, int iters, cudaStream_t st) {
+  if (fp64)
+    k_fma_peak<double><<<blocks, 256, 0, st>>>((double*)sink, iters, 0.9999999, 1e-9);
+  else
+    k_fma_peak<float><<<blocks, 256, 0, st>>>((float*)sink, iters, 0.9999999f, 1e-9f);
+}
+
 void launch_autocorr(const double* x, int64_t n, int64_t max_lag, double* C, cudaStream_t st) {
   const int64_t grid = std::min<int64_t>(max_lag, 152 * 8);
   k_autocorr<<<(unsigned)grid, kBlock, 0, st>>>(x, n, max_lag, C);

@@ -16,6 +16,7 @@
 // zero), one thread per listed pair; the stresses are
 // (1/V) sum F_{i<-j} (x) r_ij for the contact, lubrication and pair
 // Brownian parts.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -71,12 +72,13 @@ k_pair_stress_noalloc(NoallocArgs a, double* scratch, double* out) {
       const double iL[3] = {1.0 / a.L[0], 1.0 / a.L[1], 1.0 / a.L[2]};
       min_image_f64(xj_[0] - xi_[0], xj_[1] - xi_[1], xj_[2] - xi_[2], a.L, iL, a.tilt, r, &sy);
       const double d = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+      const double id = 1.0 / d;
       const double ai = a.radii[i], aj = a.radii[j];
       const double S = ai + aj;
       const double h = d - S;
       const double xi = 2.0 * h / S;
       if (xi <= a.xi_max) {
-        const double n[3] = {r[0] / d, r[1] / d, r[2] / d};
+        const double n[3] = {r[0] * id, r[1] * id, r[2] * id};
         const double Ui[3] = {a.U[3 * i], a.U[3 * i + 1], a.U[3 * i + 2]};
         const double Uj[3] = {a.U[3 * j], a.U[3 * j + 1], a.U[3 * j + 2]};
         const double Wi[3] = {a.W[3 * i], a.W[3 * i + 1], a.W[3 * i + 2]};
@@ -86,7 +88,8 @@ k_pair_stress_noalloc(NoallocArgs a, double* scratch, double* out) {
         PairOut<double> o;
         if (a.lubrication) {
           const double xi_e = xi < a.xi_min ? a.xi_min : xi;
-          const Res8<double> R = resistances<double>(a.eta, ai, aj, xi_e, log(1.0 / xi_e));
+          const double ixi = 1.0 / xi_e;
+          const Res8<double> R = resistances_rcp(a.eta, ai, aj, ixi, log(ixi));
           double g[6] = {0, 0, 0, 0, 0, 0};
           // tags are the caller's indices
           if (NOISE) gauss6_f64(a.key0, a.key1, a.k, (uint32_t)i, (uint32_t)j, g);
@@ -119,20 +122,38 @@ k_pair_stress_noalloc(NoallocArgs a, double* scratch, double* out) {
   }
   __syncthreads();
   if (last) {
+    // warp w sums components w, w + 8, w + 16, w + 24: its lanes stride over
+    // the block partials (lane l takes blocks l, l + 32, ...), then a fixed
+    // shuffle tree adds the 32 lane sums, so the order does not depend on
+    // scheduling
     __threadfence();
-    for (int c = threadIdx.x; c < kVirLen; c += blockDim.x) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c = warp; c < kVirLen; c += kBlock / 32) {
       double s = 0.0;
-      for (unsigned int b = 0; b < gridDim.x; ++b)
+      for (unsigned int b = lane; b < gridDim.x; b += 32)
         s += *(volatile double*)&partial[(int64_t)b * kVirLen + c];
-      out[c] = s * a.inv_V;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) out[c] = s * a.inv_V;
     }
     if (threadIdx.x == 0) *ticket = 0u;
   }
 }
 
 namespace {
+// device address of the scratch array in each CUDA context seen so far,
+// keyed by the context's unique ID (never reused within a process): the
+// address belongs to a context, so a call made in another context (after a
+// device reset, or in a context the caller created) looks it up again
+struct CtxAddr {
+  unsigned long long id;
+  double* ptr;
+};
 std::mutex g_noalloc_mutex;
-double* g_noalloc_ptr[64] = {nullptr};
+CtxAddr g_noalloc_ptr[64] = {};
+int g_noalloc_n = 0;
+CUresult (*g_ctx_get_current)(CUcontext*) = nullptr;
+CUresult (*g_ctx_get_id)(CUcontext, unsigned long long*) = nullptr;
 }  // namespace
 
 }  // namespace susp
@@ -165,22 +186,46 @@ extern "C" int susp_pair_stress_noalloc(int64_t N, const double* x, const double
   if (!(dt > 0) || !(p->kT >= 0) || !(box[0] > 0 && box[1] > 0 && box[2] > 0))
     return noalloc_fail(SUSP_EINVAL, "need dt > 0, kT >= 0 and a positive box");
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0)
     return noalloc_fail(SUSP_ENODEV, "no usable CUDA device");
+  // cudaFree(0) makes the device's primary context current if no context is
+  // (it frees nothing)
+  if (cudaFree(nullptr) != cudaSuccess)
+    return noalloc_fail(SUSP_ENODEV, "no usable CUDA context");
   double* scratch = nullptr;
   {
-    // once per device, with that device current: the device address of the
+    // once per CUDA context, with it current: the device address of the
     // static array (its name in host code is only a host-side stand-in)
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+      void* f1 = nullptr;
+      void* f2 = nullptr;
+      cudaDriverEntryPointQueryResult q1, q2;
+      if (cudaGetDriverEntryPoint("cuCtxGetCurrent", &f1, cudaEnableDefault, &q1) != cudaSuccess ||
+          q1 != cudaDriverEntryPointSuccess || !f1 ||
+          cudaGetDriverEntryPoint("cuCtxGetId", &f2, cudaEnableDefault, &q2) != cudaSuccess ||
+          q2 != cudaDriverEntryPointSuccess || !f2)
+        return noalloc_fail(SUSP_ECUDA, "cuCtxGetCurrent / cuCtxGetId are not available");
+      g_ctx_get_current = reinterpret_cast<CUresult (*)(CUcontext*)>(f1);
+      g_ctx_get_id = reinterpret_cast<CUresult (*)(CUcontext, unsigned long long*)>(f2);
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx || g_ctx_get_id(ctx, &id) != CUDA_SUCCESS)
+      return noalloc_fail(SUSP_ECUDA, "no current CUDA context");
+    for (int c = 0; c < g_noalloc_n; ++c)
+      if (g_noalloc_ptr[c].id == id) scratch = g_noalloc_ptr[c].ptr;
+    if (!scratch) {
       void* ptr = nullptr;
       const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
       if (e != cudaSuccess || !ptr)
         return noalloc_fail(SUSP_ECUDA,
                             std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
-      g_noalloc_ptr[dev] = static_cast<double*>(ptr);
+      scratch = static_cast<double*>(ptr);
+      // a full table starts over (the entries are only a cache)
+      if (g_noalloc_n == 64) g_noalloc_n = 0;
+      g_noalloc_ptr[g_noalloc_n++] = CtxAddr{id, scratch};
     }
-    scratch = g_noalloc_ptr[dev];
   }
   cudaStream_t st = (cudaStream_t)stream;
   // the ticket must start at zero (a previous call leaves it at zero, an

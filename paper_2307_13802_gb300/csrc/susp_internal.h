@@ -267,6 +267,7 @@ void launch_pair_mixed(const Arrays& A, const BlockMap& bm, const StepArgs& s,
                        int tpp, cudaStream_t st);
 void launch_autocorr(const double* x, int64_t n, int64_t max_lag, double* C,
                      cudaStream_t st);
+void launch_fma_peak(int fp64, void* sink, int blocks, int iters, cudaStream_t st);
 // ppar: the pair_partial_w buffer to read (mixed path)
 void launch_reduce_stress(const Arrays& A, const BlockMap& bm, int sample_pair,
                           int sample_kin, int ppar, cudaStream_t st);
