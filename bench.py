@@ -48,9 +48,18 @@ NCU_TRAFFIC = {
     # ncu --set full on the 1M bench workload: DRAM read + write per launch / N
     # issue_active: fraction of cycles the kernel issued an instruction (the
     # pair kernel is bound by issue and latency, not by DRAM)
-    "k_pair_mixed": {"bytes_per_sphere": 314.386, "source_sha": "2cdd6539e7f8d9fc",
-                     "issue_active": 0.779, "dram_throughput": 0.200},
+    "k_pair_mixed": {"bytes_per_sphere": 316.797, "source_sha": "34e9ae9eab9a9df3",
+                     "issue_active": 0.761, "dram_throughput": 0.211},
     "k_integrate_mixed": {"bytes_per_sphere": 268.032, "source_sha": "a36871f83c3d4e1f"},
+}
+
+# Double-precision floating-point operations per launch of the FP64 pair
+# kernel, per sphere, from one ncu capture on the 1M bench workload: 2 per
+# DFMA plus 1 per DADD and DMUL (smsp__sass_thread_inst_executed_op_d{fma,add,
+# mul}_pred_on.sum); reported only while the source is unchanged.
+NCU_FP64_FLOPS = {
+    # 916.4 M DADD + 782.3 M DFMA + 996.9 M DMUL thread instructions per launch
+    "k_pair_fp64": {"flops_per_sphere": 3477.806, "source_sha": "5ce41fae482b9884"},
 }
 
 
@@ -83,6 +92,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true",
                     help="skip the FP64-path comparison line")
+    ap.add_argument("--phases", action="store_true",
+                    help="time the mixed pair kernel's template variants (noise, friction, "
+                         "stress sampling, lubrication switched off one at a time) on the "
+                         "bench workload and print one JSON line")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other workloads (FP64 10k, 256 replicas, 8M) and the "
                          "mixed-vs-FP64 accuracy run")
@@ -174,6 +187,14 @@ def algorithmic_bytes(family: str, precision: str, K: float, c: float, fric: boo
     if family == "integrate":
         return 244.0 if precision == "mixed" else 196.0
     return 0.0
+
+
+def rebuild_bytes(K: float, passes: int = 2) -> float:
+    """Algorithmic bytes per sphere of one neighbour rebuild: read the
+    position (24) and write the cell key (4) and permutation (4), `passes`
+    counting-sort passes over 4-byte keys, permute the particle records once
+    (read and write 150), write the list (4K)."""
+    return 24.0 + 8.0 + 8.0 * passes + 150.0 + 4.0 * K
 
 
 def layout_bytes(family: str, precision: str, K: float, c: float, fric: bool) -> float:
@@ -310,6 +331,15 @@ def run_ours(args, rank, world, local_rank, dist):
                     "contacts_per_sphere": round(c, 3)}
         if ncu:
             roofline["ncu"] = ncu
+    rebuild_roof = None
+    if prof["rebuild"]["launches"] > 0:
+        rb = rebuild_bytes(K) * N
+        ach = rb / (prof["rebuild"]["ms_per_launch"] * 1e-3) / 1e9
+        rebuild_roof = {"bound": "hbm", "kernels": "cell keys, counting sort, permutation, "
+                        "list, history carry-over, mirrors", "achieved": round(ach, 1),
+                        "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
+                        "bytes_per_sphere": round(rebuild_bytes(K), 3),
+                        "ms_per_rebuild": round(prof["rebuild"]["ms_per_launch"], 4)}
     breakdown = {f: {"ms_per_launch": round(v["ms_per_launch"], 5),
                      "launches": v["launches"], "ms": round(v["ms"], 3)}
                  for f, v in prof.items()}
@@ -345,9 +375,26 @@ def run_ours(args, rank, world, local_rank, dist):
         e1.record(stream)
         e1.synchronize()
         ms64 = e0.elapsed_time(e1)
+        prof64 = s64.profile(2, p["dt"])
         fp64 = {"value": round(world * N * n64 / (ms64 / 1e3), 1),
                 "ms_per_timestep": round(ms64 / n64, 4),
-                "speedup_of_mixed": round(value / (world * N * n64 / (ms64 / 1e3)), 2)}
+                "speedup_of_mixed": round(value / (world * N * n64 / (ms64 / 1e3)), 2),
+                "pair_ms_per_launch": round(prof64["pair"]["ms_per_launch"], 4)}
+        try:
+            pk = susp.measure_peaks()
+        except susp.SuspError:
+            pk = None
+        rec = NCU_FP64_FLOPS.get("k_pair_fp64")
+        if pk and rec and rec.get("source_sha") == _src_hash("k_pair_fp64.cu"):
+            fl = rec["flops_per_sphere"] * N
+            ach = fl / (prof64["pair"]["ms_per_launch"] * 1e-3) / 1e9
+            fp64["roofline"] = {"bound": "alu", "kernel": "k_pair_fp64", "unit": "GFLOP/s",
+                                "achieved": round(ach, 1), "peak": round(pk["fp64_gflops"], 1),
+                                "peak_kind": "measured FP64 multiply-add microbenchmark",
+                                "frac": round(ach / pk["fp64_gflops"], 4),
+                                "flops_per_launch": fl}
+        elif pk:
+            fp64["fp64_peak_gflops"] = round(pk["fp64_gflops"], 1)
         s64.close()
 
     legs = {}
@@ -369,10 +416,8 @@ def run_ours(args, rank, world, local_rank, dist):
             "bidisperse-10k-phi0.56-pe10-mu1 (fp64)": leg(lambda: run_single(
                 susp, workloads.named("bidisperse-10k-phi0.56"), "fp64", stream, 100, 5)),
             "batched-256-replicas (mixed)": leg(lambda: run_batched(susp, stream)),
-            "polydisperse-8M-phi0.60-pe100-mu1 (mixed)": leg(lambda: run_single(
-                susp, workloads.named("polydisperse-8M-phi0.60-pe100-mu1"), "mixed", stream,
-                100, 3)),
         }
+        legs["scaling_polydisperse_phi0.60_pe100_mu1"] = leg(lambda: run_scaling(susp, stream))
 
     launches = int(info1["launches"] - info0["launches"])
     out = {
@@ -385,11 +430,13 @@ def run_ours(args, rank, world, local_rank, dist):
         "config": {"workload": WORKLOAD, "N": N, "phi": 0.58, "Pe": 1000.0, "mu": 1.0,
                    "precision": args.precision, "timesteps_per_step": args.inner,
                    "dt": p["dt"], "box": round(w.L, 4), "parallelism": f"replicas{world}",
-                   "l2": "inputs larger than L2 (state + list > 300 MB)"},
+                   "l2": "inputs larger than L2 (state + list > 300 MB)",
+                   "stress_sample_every": 1},
         "e2e": {"value": round(e2e_val, 1), "unit": METRIC,
                 "h2d_bytes_per_step": 3 * 3 * 8 * N, "d2h_bytes_per_step": 58 * 8},
         "gpu_launches": launches,
         "roofline": roofline,
+        "rebuild_roofline": rebuild_roof,
         "kernel_breakdown": breakdown,
         "eta_r": round(float(sig["eta_r"]), 4),
         "neighbour_builds": int(info1["nbuilds"] - info0["nbuilds"]),
@@ -441,6 +488,103 @@ def run_single(susp, w, precision, stream, inner, steps, warmup=1):
     return {"value": round(w.N * inner * steps / (ms / 1e3), 1), "N": w.N,
             "precision": precision, "timesteps": inner * steps,
             "ms_per_timestep": round(ms / (inner * steps), 4), "eta_r": round(float(eta), 4)}
+
+
+def run_scaling(susp, stream, inner=100, steps=3):
+    """Linear-in-N scaling of the mixed path: one seeded periodic packing of
+    15,625 polydisperse spheres (radii U[1, 1.4], phi 0.60, Pe 100, mu 1)
+    replicated 4x4x4, 4x4x8, 4x8x8 and 8x8x8 times (1M, 2M, 4M, 8M spheres,
+    the same local structure), each timed over `steps` calls of `inner`
+    timesteps after one warm-up call; with the pair kernel's time per launch
+    and its fraction of the HBM roofline from susp_profile."""
+    import workloads
+    hbm, peak_kind = peaks()
+    out = {}
+    for ks in ((4, 4, 4), (4, 4, 8), (4, 8, 8), (8, 8, 8)):
+        rs, box, x, U, W, p = workloads.scaled_tiles(15625, ks, 0.60, 100.0, 1.0, poly=True,
+                                                     pack_seed=1005, dyn_seed=2005)
+        N = len(rs)
+        s = susp.System(rs, box, precision="mixed", eta=p["eta"], rho=p["rho"], kn=p["kn"],
+                        kt=p["kt"], mu=p["mu"], skin=p["skin"], shear_rate=p["shear_rate"],
+                        kT=p["kT"], seed=p["seed"], dt=p["dt"])
+        s.set_stream(stream.cuda_stream)
+        s.set_state(x, U, W)
+        s.step(inner, p["shear_rate"], p["kT"], p["dt"], p["seed"])
+
+        def run():
+            for _ in range(steps):
+                s.step(inner, p["shear_rate"], p["kT"], p["dt"], p["seed"])
+        ms = _timed(stream, run)
+        prof = s.profile(inner, p["dt"])
+        info = s.info()
+        ij, _ = s.history()
+        K, c = info["npairs"] / N, len(ij) / N
+        pb = algorithmic_bytes("pair", "mixed", K, c, True)
+        pair_ms = prof["pair"]["ms_per_launch"]
+        # one explicit rebuild (the kernels a due rebuild runs), timed alone
+        rb_ms = _timed(stream, s.build_neighbors)
+        rbb = rebuild_bytes(K)
+        out[f"{N // 1000000}M"] = {
+            "N": N, "tiles": list(ks), "value": round(N * inner * steps / (ms / 1e3), 1),
+            "ms_per_timestep": round(ms / (inner * steps), 4),
+            "pair_ms_per_launch": round(pair_ms, 5),
+            "pair_hbm_frac": round(pb * N / (pair_ms * 1e-3) / 1e9 / hbm, 4),
+            "rebuild_ms": round(rb_ms, 4),
+            "rebuild_hbm_frac": round(rbb * N / (rb_ms * 1e-3) / 1e9 / hbm, 4),
+            "half_list_slots_per_sphere": round(K, 3), "contacts_per_sphere": round(c, 3)}
+        s.close()
+    # linear in N: the same particle-steps/s at every size
+    v = [out[k]["value"] for k in out]
+    out["value_spread"] = round(max(v) / min(v) - 1.0, 4)
+    out["peak_kind"] = peak_kind
+    return out
+
+
+PHASE_VARIANTS = (
+    ("full", {}),
+    ("no_noise", dict(noise=0)),
+    ("no_friction", dict(mu=0.0, kt=0.0)),
+    ("no_sampling", dict(sample_every=1000)),
+    ("no_noise_no_sampling", dict(noise=0, sample_every=1000)),
+    ("no_noise_no_friction_no_sampling", dict(noise=0, mu=0.0, kt=0.0, sample_every=1000)),
+    ("no_lubrication", dict(lubrication=0)),
+)
+
+
+def run_phases(inner: int = 100, warm: int = 200):
+    """Where the pair kernel's time goes: the bench workload (1M spheres,
+    mixed) with one term after another switched off, each kernel family
+    timed per launch by susp_profile after `warm` steps.  The differences
+    are the costs of the pair noise (Philox + Box-Muller + the Brownian
+    algebra), the tangential history, the stress sampling (virials and their
+    reductions) and the lubrication (resistances + pair noise)."""
+    import torch
+
+    import paper_2307_13802_gb300 as susp
+    import workloads
+    w = workloads.named(WORKLOAD)
+    p = w.params
+    stream = torch.cuda.Stream()
+    out = {}
+    for name, kw in PHASE_VARIANTS:
+        args = dict(precision="mixed", eta=p["eta"], rho=p["rho"], kn=p["kn"], kt=p["kt"],
+                    mu=p["mu"], skin=p["skin"], shear_rate=p["shear_rate"], kT=p["kT"],
+                    seed=p["seed"], dt=p["dt"])
+        args.update(kw)
+        s = susp.System(w.radii, w.box, **args)
+        s.set_stream(stream.cuda_stream)
+        s.set_state(w.x, w.U, w.W)
+        s.step(warm, p["shear_rate"], p["kT"], p["dt"], p["seed"])
+        prof = s.profile(inner, p["dt"])
+        out[name] = {f: round(v["ms_per_launch"], 5) for f, v in prof.items() if v["launches"]}
+        s.close()
+    full = out["full"]["pair"]
+    costs = {"pair_noise": full - out["no_noise"]["pair"],
+             "tangential_history": full - out["no_friction"]["pair"],
+             "stress_sampling": full - out["no_sampling"]["pair"],
+             "base": out["no_noise_no_friction_no_sampling"]["pair"]}
+    return {"workload": WORKLOAD, "metric": "ms per launch", "variants": out,
+            "pair_cost_ms": {k: round(v, 5) for k, v in costs.items()}}
 
 
 def run_batched(susp, stream, inner=100, steps=3):
@@ -533,46 +677,78 @@ def cpu_sample_workload():
                           pack_seed=ps, dyn_seed=ds)
 
 
-def run_cpu_baseline(timesteps: int = 400):
+def cpu_model() -> str:
+    """The host CPU's model name as the OS reports it."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def _oracle_worker(job):
+    """One host core: the oracle on its own copy of the sample workload,
+    `warm` untimed steps then `timed` timed steps; returns the seconds."""
+    radii, box, params, x, U, W, warm, timed = job
     import oracle
-    w = cpu_sample_workload()
-    o = oracle.System(w.radii, w.box, **w.params)
-    o.set_state(w.x, w.U, w.W)
-    o.step(1)                       # list build and setup evaluation
+    o = oracle.System(radii, box, **params)
+    o.set_state(x, U, W)
+    o.step(max(1, warm))            # list build, setup evaluation, warm-up
     t0 = time.perf_counter()
-    o.step(timesteps)
-    dt = time.perf_counter() - t0
-    return {"value": round(w.N * timesteps / dt, 1), "unit": METRIC, "cores": 1,
-            "kind": "oracle",
-            "sample": f"{w.N}-sphere periodic tile of the same packing recipe, "
-                      f"{timesteps} timesteps, serial FP64 oracle with O(N^2) list builds"}
+    o.step(timed)
+    return time.perf_counter() - t0
+
+
+def run_oracle_on_cores(warm: int, timed: int, cores: int = 0):
+    """The serial oracle on every host core at once, each core stepping its
+    own copy of the sample workload (independent replicas: the oracle itself
+    is unchanged).  Returns (particle-steps/s over all cores, seconds of the
+    slowest core, cores, N)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    w = cpu_sample_workload()
+    cores = cores or os.cpu_count() or 1
+    job = (w.radii, w.box, w.params, w.x, w.U, w.W, warm, timed)
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
+        secs = list(ex.map(_oracle_worker, [job] * cores))
+    slowest = max(secs)
+    return cores * w.N * timed / slowest, slowest, cores, w.N
+
+
+def run_cpu_baseline(timesteps: int = 200):
+    value, secs, cores, n = run_oracle_on_cores(1, timesteps)
+    return {"value": round(value, 1), "unit": METRIC, "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(),
+            "sample": f"{n}-sphere periodic tile of the same packing recipe, {timesteps} "
+                      f"timesteps on each of {cores} cores at once (one serial FP64 oracle "
+                      f"per core on its own copy, O(N^2) list builds); {secs:.1f} s"}
 
 
 def run_reference(args):
-    import oracle
-    w = cpu_sample_workload()
-    o = oracle.System(w.radii, w.box, **w.params)
-    o.set_state(w.x, w.U, w.W)
     inner = 20
-    o.step(1)
-    for _ in range(args.warmup):
-        o.step(inner)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        o.step(inner)
-    dt = time.perf_counter() - t0
-    value = w.N * inner * args.steps / dt
-    sample = (f"{w.N}-sphere periodic tile of the {WORKLOAD} packing, {inner} timesteps "
-              f"per bench step, serial FP64 oracle")
+    value, secs, cores, n = run_oracle_on_cores(args.warmup * inner, args.steps * inner)
+    sample = (f"{n}-sphere periodic tile of the {WORKLOAD} packing, {inner} timesteps per "
+              f"bench step on each of {cores} cores at once (one serial FP64 oracle per "
+              f"core on its own copy)")
     return {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": METRIC,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "ms_per_step": round(secs / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic seeded packing (no dataset)",
-            "config": {"workload": WORKLOAD, "N": w.N, "timesteps_per_step": inner,
-                       "parallelism": "cpu"},
-            "cpu_baseline": {"value": round(value, 1), "unit": METRIC, "cores": 1,
-                             "kind": "oracle", "sample": sample},
+            "config": {"workload": WORKLOAD, "N": n, "timesteps_per_step": inner,
+                       "parallelism": f"cpu{cores}"},
+            "cpu_baseline": {"value": round(value, 1), "unit": METRIC, "cores": cores,
+                             "kind": "oracle", "cpu_model": cpu_model(), "sample": sample},
             "e2e": {"value": round(value, 1), "unit": METRIC, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -585,6 +761,10 @@ def main():
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
+        return
+    if args.phases:
+        if rank == 0:
+            print(json.dumps(run_phases()), flush=True)
         return
     dist = None
     if world > 1:

@@ -150,12 +150,20 @@ def base_params(pe: float, mu: float, seed: int, rate: float = 1.0,
 
 def tile_packing(radii, x, L: float, k: int):
     """Replicate a periodic packing k x k x k times (box edge k L)."""
+    rs, xs, box = tile_packing_box(radii, x, L, (k, k, k))
+    return rs, xs, L * k
+
+
+def tile_packing_box(radii, x, L: float, ks):
+    """Replicate a periodic packing of a cubic box of edge L kx x ky x kz
+    times; returns radii, positions and the box edges (kx L, ky L, kz L)."""
+    kx, ky, kz = ks
     n = len(radii)
-    shifts = np.array([(i, j, l) for l in range(k) for j in range(k)
-                       for i in range(k)], dtype=np.float64) * L
-    xs = (x[None, :, :] + shifts[:, None, :]).reshape(n * k ** 3, 3)
-    rs = np.tile(radii, k ** 3)
-    return rs, np.ascontiguousarray(xs), L * k
+    shifts = np.array([(i, j, l) for l in range(kz) for j in range(ky)
+                       for i in range(kx)], dtype=np.float64) * L
+    xs = (x[None, :, :] + shifts[:, None, :]).reshape(n * kx * ky * kz, 3)
+    rs = np.tile(radii, kx * ky * kz)
+    return rs, np.ascontiguousarray(xs), np.array([kx * L, ky * L, kz * L])
 
 
 def make(N: int, phi: float, pe: float, mu: float, *, poly: bool = False,
@@ -192,6 +200,23 @@ WORKLOADS = {
         N=8_000_000, phi=0.60, pe=100.0, mu=1.0, poly=True, steps=2000, tile=8,
         seeds=(1005, 2005)),
 }
+
+
+def scaled_tiles(tile_n: int, ks, phi: float, pe: float, mu: float, *, poly: bool,
+                 pack_seed: int, dyn_seed: int, name: str = "tiled", rate: float = 1.0):
+    """One seeded periodic packing of tile_n spheres replicated kx x ky x kz
+    times: systems of different sizes with the same local structure (for
+    scaling in N).  Returns (radii, box[3], x, U, W, params)."""
+    n = tile_n
+    radii = polydisperse_radii(n, pack_seed) if poly else bidisperse_radii(n, pack_seed)
+    L = box_for_phi(radii, phi)
+    x, _ = packing(radii, L, pack_seed + 1)
+    rs, xs, box = tile_packing_box(radii, x, L, ks)
+    U = np.zeros_like(xs)
+    U[:, 0] = rate * (xs[:, 1] - 0.5 * box[1])
+    W = np.zeros_like(xs)
+    W[:, 2] = -0.5 * rate
+    return rs, box, xs, U, W, base_params(pe, mu, dyn_seed, rate=rate)
 
 
 def named(name: str, **override) -> Workload:
