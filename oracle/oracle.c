@@ -340,12 +340,15 @@ static void wrap_particle(o_sys* s, int i) {
   double Ly = s->L[1];
   double dUx = s->p.shear_rate * Ly;
   if (!isfinite(x[0] + x[1] + x[2])) return;
-  while (x[1] >= Ly) { x[1] = x[1] - Ly; x[0] = x[0] - s->tilt; U[0] = U[0] - dUx; }
-  while (x[1] < 0.0) { x[1] = x[1] + Ly; x[0] = x[0] + s->tilt; U[0] = U[0] + dUx; }
-  while (x[0] >= s->L[0]) x[0] = x[0] - s->L[0];
-  while (x[0] < 0.0) x[0] = x[0] + s->L[0];
-  while (x[2] >= s->L[2]) x[2] = x[2] - s->L[2];
-  while (x[2] < 0.0) x[2] = x[2] + s->L[2];
+  /* a sphere moves far less than a box edge per step; the loops stop after
+   * 64 images so that a run that has blown up ends instead of spinning */
+  int g = 0;
+  while (x[1] >= Ly && g < 64) { x[1] = x[1] - Ly; x[0] = x[0] - s->tilt; U[0] = U[0] - dUx; ++g; }
+  while (x[1] < 0.0 && g < 64) { x[1] = x[1] + Ly; x[0] = x[0] + s->tilt; U[0] = U[0] + dUx; ++g; }
+  while (x[0] >= s->L[0] && g < 64) { x[0] = x[0] - s->L[0]; ++g; }
+  while (x[0] < 0.0 && g < 64) { x[0] = x[0] + s->L[0]; ++g; }
+  while (x[2] >= s->L[2] && g < 64) { x[2] = x[2] - s->L[2]; ++g; }
+  while (x[2] < 0.0 && g < 64) { x[2] = x[2] + s->L[2]; ++g; }
 }
 
 /* ------------------------------------------------------------------ */
