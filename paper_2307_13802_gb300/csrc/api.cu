@@ -728,7 +728,17 @@ int run_steps(susp_t* h, int64_t n_steps, double dt) {
   while (done < n_steps) {
     const int64_t left = n_steps - done;
     const bool graphs_ok = h->p0.use_graphs && (chunk % h->p0.sample_every == 0);
-    if (graphs_ok && left >= chunk && (h->steps_done % h->p0.sample_every) == 0) {
+    const int64_t phase = h->steps_done % h->p0.sample_every;
+    if (graphs_ok && left >= chunk && phase != 0) {
+      // eager steps up to the next sampling boundary, where the captured
+      // chunks (sampled at their first step) line up again
+      const int64_t m = std::min<int64_t>(left, h->p0.sample_every - phase);
+      enqueue_steps(h, h->steps_done, m, dt, st, false, nullptr);
+      done += m;
+      h->steps_done += m;
+      continue;
+    }
+    if (graphs_ok && left >= chunk && phase == 0) {
       GraphChunk* g = nullptr;
       rc = get_graph(h, chunk, dt, &g);
       if (rc) {

@@ -219,3 +219,30 @@ def test_stress_samples_do_not_depend_on_how_steps_are_grouped(susp, sample_ever
     assert np.abs(x1 - x2).max() <= 1e-7
     for key in ("contact", "lubrication", "brownian", "kinetic", "kinetic_rot", "structural"):
         assert _relerr(s1[key], s2[key]) <= 1e-5, key
+
+
+def test_graph_replay_resumes_after_unaligned_calls_when_sampling_sparsely(susp, record):
+    """With the stress sampled every 8th step, calls of 100 steps end off the
+    sampling grid; the next call must run eager steps up to the grid and then
+    replay captured chunks again, with the samples where an eager run puts
+    them."""
+    w = workloads.make(6000, 0.55, 100.0, 1.0, pack_seed=95, dyn_seed=96)
+    p = w.params
+    res = []
+    for graphs in (1, 0):
+        g = _sys(susp, w, "mixed", sample_every=8, use_graphs=graphs)
+        g.set_state(w.x, w.U, w.W)
+        steps0 = None
+        for call in range(3):
+            g.step(100, p["shear_rate"], p["kT"], p["dt"], p["seed"])
+            if call == 0:
+                steps0 = g.info()["graph_steps"]
+        res.append((g.info(), g.stress(), g.forces()[0]))
+    (i1, s1, F1), (i0, s0, F0) = res
+    # graphs were replayed in the second and third calls too
+    assert i1["graph_steps"] >= steps0 + 2 * 64 and i0["graph_steps"] == 0
+    assert s1["samples"] == s0["samples"] == len(range(0, 300, 8))
+    record("force", _relerr(F1, F0), 1e-4)
+    assert _relerr(F1, F0) <= 1e-4
+    for key in ("contact", "lubrication"):
+        assert _relerr(s1[key], s0[key]) <= 1e-5, key
