@@ -50,7 +50,7 @@ NCU_TRAFFIC = {
     # pair kernel is bound by issue and latency, not by DRAM)
     "k_pair_mixed": {"bytes_per_sphere": 316.797, "source_sha": "34e9ae9eab9a9df3",
                      "issue_active": 0.761, "dram_throughput": 0.211},
-    "k_integrate_mixed": {"bytes_per_sphere": 268.032, "source_sha": "a36871f83c3d4e1f"},
+    "k_integrate_mixed": {"bytes_per_sphere": 265.448, "source_sha": "642ebccc2ca93352"},
 }
 
 # Double-precision floating-point operations per launch of the FP64 pair
