@@ -647,12 +647,18 @@ def run_batched(susp, stream, inner=100, steps=3):
     ms = _timed(stream, run)
     total = int(sum(sizes))
     etas = [b.stress(r)["eta_r"] for r in range(len(ws))]
+    i0 = b.info()
+    prof = b.profile(inner, dt)
+    i1 = b.info()
     b.close()
+    breakdown = {f: {"ms_per_launch": round(v["ms_per_launch"], 5), "launches": v["launches"]}
+                 for f, v in prof.items() if v["launches"]}
     return {"value": round(total * inner * steps / (ms / 1e3), 1), "replicas": len(ws),
             "particles": total, "precision": "mixed", "timesteps": inner * steps,
             "ms_per_timestep": round(ms / (inner * steps), 4),
             "finite_eta_r": bool(all(math.isfinite(e) for e in etas)),
-            "skin": skin,
+            "skin": skin, "kernel_breakdown": breakdown,
+            "rebuilds_in_profiled_steps": int(i1["nbuilds"] - i0["nbuilds"]),
             "autotune_ms_per_step": {str(k): (round(float(v), 4) if math.isfinite(v) else None)
                                      for k, v in zip(skins, trial_ms)},
             "packing_tol": 1e-2, "generation_s": round(gen_s, 1)}
