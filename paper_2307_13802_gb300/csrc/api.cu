@@ -182,6 +182,11 @@ int common_create(susp_t** out, int32_t R, const int64_t* N_r,
   int64_t N = 0;
   for (int r = 0; r < R; ++r) N += N_r[r];
   if (N >= (int64_t)1 << 31) { g_create_error = "too many spheres"; return SUSP_EINVAL; }
+  if (p_r[0].precision == SUSP_MIXED && N > kNbrIndexMask) {
+    // list entries keep the partner's home-cell offset in their top bits
+    g_create_error = "the mixed path holds at most 134,217,727 spheres";
+    return SUSP_EINVAL;
+  }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
     g_create_error = "no CUDA device";

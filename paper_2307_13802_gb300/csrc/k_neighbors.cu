@@ -266,7 +266,8 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Arrays A, StepArgs s, dou
             const float rc = fmaxf(fmaxf(S * fac, S * rfac), S + shell * fmaxf(P.w, Q.w)) +
                              skin + margin + 1e-5f * S;
             if (!(rx * rx + ry * ry + rz * rz < rc * rc)) continue;
-            if (cnt < kmax) row[(int64_t)cnt * Np] = q;
+            const int code = (dx + 1) * 3 + (dy + 1) + 9 * (dz + 1);
+            if (cnt < kmax) row[(int64_t)cnt * Np] = q | (code << kNbrIndexBits);
             ++cnt;
           }
         }
@@ -348,7 +349,7 @@ __global__ void __launch_bounds__(kBlock) k_remap_history(Arrays A) {
   const float margin = 1e-6f * fmaxf(Lf[0], fmaxf(Lf[1], Lf[2]));
   const double4_32a P = A.mixed ? double4_32a{} : A.pos[nxt][p];
   for (int sl = 0; sl < nn; ++sl) {
-    const int q = A.nbr[nxt][(int64_t)sl * Np + p];
+    const int q = A.nbr[nxt][(int64_t)sl * Np + p] & kNbrIndexMask;
     if (A.mixed) {
       const float4 Q = reinterpret_cast<const float4*>(A.pos[nxt])[2 * q];
       float ry = Q.y - Pf.y, rx = Q.x - Pf.x, rz = Q.z - Pf.z;
@@ -370,11 +371,11 @@ __global__ void __launch_bounds__(kBlock) k_remap_history(Arrays A) {
     int row = -1, slot = -1;
     const int n1 = A.nnb[cur][op];
     for (int t = 0; t < n1; ++t)
-      if (A.nbr[cur][(int64_t)t * Np + op] == oq) { row = op; slot = t; break; }
+      if ((A.nbr[cur][(int64_t)t * Np + op] & kNbrIndexMask) == oq) { row = op; slot = t; break; }
     if (row < 0) {
       const int n2 = A.nnb[cur][oq];
       for (int t = 0; t < n2; ++t)
-        if (A.nbr[cur][(int64_t)t * Np + oq] == op) { row = oq; slot = t; break; }
+        if ((A.nbr[cur][(int64_t)t * Np + oq] & kNbrIndexMask) == op) { row = oq; slot = t; break; }
     }
     if (row < 0) continue;
     if (!((A.cmsk[cur][row] >> slot) & 1ull)) continue;

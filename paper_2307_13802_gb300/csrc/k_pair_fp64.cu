@@ -92,7 +92,7 @@ k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
     const int64_t hstride = (int64_t)A.kmax * Np;
 
     for (int sl = 0; sl < nn; ++sl) {
-      const int q = row[(int64_t)sl * Np];
+      const int q = row[(int64_t)sl * Np] & kNbrIndexMask;
       const double4_32a Q = A.pos[cur][q];
       double rpq[3], sy;
       min_image_f64(Q.x - P.x, Q.y - P.y, Q.z - P.z, L, iL, tilt, rpq, &sy);

@@ -10,8 +10,10 @@
 //     prefix sum of the row lengths); lane l takes items l, l+32, ...  Rows
 //     of uneven length therefore cost no idle lanes.
 //   - Geometry: r = (posm_q - posm_p) + H(t) dc / nc with the home-cell
-//     difference dc in {-1, 0, 1}^3 unpacked from the mirrors; pairs beyond
-//     the lubrication cutoff are rejected on |r|^2 before any square root.
+//     difference dc in {-1, 0, 1}^3 taken from the top bits of the list
+//     entry (the stencil offset the list build found the partner at); pairs
+//     beyond the lubrication cutoff are rejected on |r|^2 before any square
+//     root.
 //   - Accumulation: the owner's share goes to shared-memory float
 //     accumulators (one vector reduction per sphere at the end), the
 //     partner's share straight to its float4 accumulator with one
@@ -122,16 +124,6 @@ __device__ __forceinline__ void df_diff_shift(float qh, float ql, float ph, floa
   fast_two_sum(s2, lo, rh, rl);
 }
 
-__device__ __forceinline__ void unpack_cell(int v, int& cx, int& cy, int& cz) {
-  cx = v & 1023;
-  cy = (v >> 10) & 1023;
-  cz = (v >> 20) & 1023;
-}
-
-__device__ __forceinline__ int wrap_dc(int d, int n) {
-  return d > 1 ? d - n : (d < -1 ? d + n : d);
-}
-
 // Sums v[0..31] over the 32 lanes of a warp and leaves the total of
 // component l in lane l: five halving stages, in each of which a lane keeps
 // one half of its components and adds the partner's copy of that half
@@ -200,7 +192,6 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   const float c = RP.noise_cf;
   const float cwx = RP.cwf[0], cwy = RP.cwf[1], cwz = RP.cwf[2], ctilt = RP.ctilt_f;
   const float cw1h = RP.cw_hi[1], cw1l = RP.cw_lo[1], cw2h = RP.cw_hi[2], cw2l = RP.cw_lo[2];
-  const int ncx = RP.nc[0], ncy = RP.nc[1], ncz = RP.nc[2];
   const uint32_t key0 = RP.key0, key1 = RP.key1;
   const int t0 = (int)RP.p0;
   const int64_t Np = A.Npad;
@@ -498,7 +489,7 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
       n1 = 32; f1 = qn1 - 32;
     } else if (base < total) {
       const int t = base + lane;
-      const int o = o_n, sl = sl_n, q = q_n;
+      const int o = o_n, sl = sl_n, qe = q_n;
       const unsigned long long ocm = FRIC ? __shfl_sync(kFull, cm_own, o) : 0ull;
       if (base + 32 < total) locate(base + 32);
       bool keep = false, touch = false;
@@ -506,13 +497,15 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
       float gq[6];
       if (t < total) {
         const int po = pb + warp * 32 + o;
+        const int q = qe & kNbrIndexMask;
         const float4 P = __ldg(PM + 2 * po), Q = __ldg(PM + 2 * q);
         const float4 Pl = __ldg(PM + 2 * po + 1), Ql = __ldg(PM + 2 * q + 1);
-        int pcx, pcy, pcz, qcx, qcy, qcz;
-        unpack_cell(__float_as_int(__ldg(&OM[po].w)), pcx, pcy, pcz);
-        unpack_cell(__float_as_int(__ldg(&OM[q].w)), qcx, qcy, qcz);
-        const int dcx = wrap_dc(qcx - pcx, ncx), dcy = wrap_dc(qcy - pcy, ncy),
-                  dcz = wrap_dc(qcz - pcz, ncz);
+        // the partner's home cell relative to the owner's, from the entry's
+        // top bits: code = 3 (dcx + 1) + (dcy + 1) + 9 (dcz + 1) < 27, split
+        // by multiply-shift divisions exact on these ranges (code / 9, c9 / 3)
+        const int code = (int)((unsigned)qe >> kNbrIndexBits);
+        const int dz1 = (code * 57) >> 9, c9 = code - 9 * dz1, dx1 = (c9 * 11) >> 5;
+        const int dcx = dx1 - 1, dcy = c9 - 3 * dx1 - 1, dcz = dz1 - 1;
         const float r0 = (Q.x - P.x) + (cwx * (float)dcx + ctilt * (float)dcy);
         const float r1 = (Q.y - P.y) + cwy * (float)dcy;
         const float r2 = (Q.z - P.z) + cwz * (float)dcz;
@@ -525,7 +518,7 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
           // separation in double-float from the cell-relative offsets, then
           // d^2 - S^2 with the cancelling squares summed error-free, and the
           // gap h = (d^2 - S^2) / (d + S)
-          const float2 shx = sShx[(dcx + 1) * 3 + (dcy + 1)];
+          const float2 shx = sShx[c9];
           const float fy = (float)dcy, fz = (float)dcz;
           float rh[3], rl[3];
           df_diff_shift(Q.x, Ql.x, P.x, Pl.x, shx.x, shx.y, rh[0], rl[0]);
@@ -587,7 +580,7 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
         const unsigned below = (1u << lane) - 1u;
         const int qk = touch ? 1 : 0;
         const int e = touch ? qn1 + __popc(m1 & below) : qn0 + __popc(m0 & below);
-        qQ[qk][warp][e] = q;
+        qQ[qk][warp][e] = qe & kNbrIndexMask;
         qM[qk][warp][e] = o | (sl << 5) | ((FRIC && ((ocm >> sl) & 1ull)) ? (1 << 12) : 0);
 #pragma unroll
         for (int c6 = 0; c6 < 6; ++c6) qG[qk][warp][c6][e] = gq[c6];

@@ -110,7 +110,7 @@ __global__ void k_list_pairs(Arrays A, const long long* __restrict__ off,
   const unsigned long long cm = with_history ? A.cmsk[cur][p] : 0ull;
   for (int sl = 0; sl < nn; ++sl) {
     if (with_history && !((cm >> sl) & 1ull)) continue;
-    const int q = A.nbr[cur][(int64_t)sl * Np + p];
+    const int q = A.nbr[cur][(int64_t)sl * Np + p] & kNbrIndexMask;
     const int tq = A.tag[cur][q];
     ij[2 * o] = tp < tq ? tp : tq;
     ij[2 * o + 1] = tp < tq ? tq : tp;

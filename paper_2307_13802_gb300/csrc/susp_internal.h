@@ -36,6 +36,13 @@ constexpr int kVirLen = 27;          // their virials: 3 components x 9 entries
 constexpr int kRepOff = 27;          // repulsion virial (9) in a block partial
 constexpr int kStrOff = 36;          // structural sums sum w n n (9), Eq. 26
 constexpr int kPartialLen = 45;      // pair entries of a block partial
+// A neighbour-list entry holds the partner's sorted index in its low 27 bits;
+// on the mixed path the top 5 bits hold the partner's home cell relative to
+// the owner's, (dcx + 1) 3 + (dcy + 1) + 9 (dcz + 1) with dc in {-1, 0, 1}^3
+// (the stencil offset the list build found it at), so the pair kernel needs
+// neither home cell.
+constexpr int kNbrIndexBits = 27;
+constexpr int kNbrIndexMask = (1 << kNbrIndexBits) - 1;
 constexpr int kKinLen = 18;          // translational + rotational kinetic
 // per-replica stress accumulator: [0, 45) pair, [45, 63) kinetic, sample counts
 constexpr int kAccStride = 72;
