@@ -58,8 +58,8 @@ NCU_TRAFFIC = {
 # DFMA plus 1 per DADD and DMUL (smsp__sass_thread_inst_executed_op_d{fma,add,
 # mul}_pred_on.sum); reported only while the source is unchanged.
 NCU_FP64_FLOPS = {
-    # 916.4 M DADD + 782.3 M DFMA + 996.9 M DMUL thread instructions per launch
-    "k_pair_fp64": {"flops_per_sphere": 3477.806, "source_sha": "5ce41fae482b9884"},
+    # 488.4 M DADD + 1,178.7 M DFMA + 638.2 M DMUL thread instructions per launch
+    "k_pair_fp64": {"flops_per_sphere": 3484.027, "source_sha": "f74580b9d3de9322"},
 }
 
 

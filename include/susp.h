@@ -127,7 +127,9 @@ void susp_default_params(susp_params* p);
 typedef struct susp_s susp_t;
 
 /* ---- lifetime ----------------------------------------------------------- */
-/* One system of N spheres with the given radii (N doubles, all > 0) in the
+/* One system of N spheres with the given radii (N doubles, all > 0; on the
+ * mixed path at most 2^27 - 1 spheres in all, the capacity of a neighbour
+ * entry's index field) in the
  * box [0,box[0]) x [0,box[1]) x [0,box[2]) with tilt 0.  Each box edge must
  * be at least three neighbour-list cutoffs, 3 * (2 a_max (1 + xi_max/2) +
  * skin).  Selects device 0 (or the current device).  Nothing is allocated on

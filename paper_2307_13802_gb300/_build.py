@@ -2,8 +2,10 @@
 
 Translation units are compiled in parallel with nvcc and linked as one shared
 library with the CUDA runtime linked statically.  The double-precision
-kernels are compiled without multiply-add contraction (``-fmad=false``) so
-that their sums and products round as written; the mixed-precision kernels
+integrator, neighbour build and utilities are compiled without multiply-add
+contraction (``-fmad=false``) so that their sums and products round as
+written (the list's cutoff decisions and the state updates then repeat the
+oracle's bit for bit); the FP64 pair kernel and the mixed-precision kernels
 use contraction.
 """
 from __future__ import annotations
@@ -23,7 +25,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
 # (source, extra flags)
 UNITS = [
     ("api.cu", []),
-    ("k_pair_fp64.cu", ["-fmad=false"]),
+    ("k_pair_fp64.cu", ["-fmad=true"]),
     ("k_integrate_fp64.cu", ["-fmad=false"]),
     ("k_neighbors.cu", ["-fmad=false"]),
     ("k_util.cu", ["-fmad=false"]),

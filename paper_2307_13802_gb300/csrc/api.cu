@@ -333,6 +333,11 @@ bool alloc_n(susp_t* h, T** p, int64_t n) {
 int allocate(susp_t* h) {
   if (h->allocated) return SUSP_OK;
   CK(cudaSetDevice(h->dev));
+  if (h->p0.precision == SUSP_FP64) {
+    const int e = prepare_pair_fp64();
+    if (e) return fail(h, SUSP_ECUDA, std::string("raising the FP64 pair kernels' shared memory: ") +
+                                          cudaGetErrorString((cudaError_t)e));
+  }
   if (!h->stream) {
     if (!h->own_stream) CK(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
     h->stream = h->own_stream;

@@ -1,12 +1,15 @@
 // k_pair_fp64.cu -- per-timestep pair force evaluation in double precision
-// (the plain FP64 path).  Compiled without multiply-add contraction so that
-// every sum and product rounds as written; the resistances and the unit
-// vector use reciprocal products in place of the printed quotients (a few
-// ulps from the printed forms), which takes the FP64 divisions, each a long
-// sequence on the FP64 pipe, from 21 to 10 per lubricated pair.
+// (the plain FP64 path).  Compiled with multiply-add contraction (a product
+// and a sum rounded once; about a sixth fewer FP64 instructions than the
+// written order), and the resistances and the unit vector use reciprocal
+// products in place of the printed quotients (a few ulps from the printed
+// forms), which takes the FP64 divisions, each a long sequence on the FP64
+// pipe, from 21 to 10 per lubricated pair.
 //
-// One thread per sphere p of the sorted order walks its half-list row.  For
-// each listed pair it forms the minimum-image gap h = |r| - (a_i + a_j) and
+// Each warp owns 32 spheres of the sorted order and flattens their half-list
+// rows into one list of items, one item per lane per pass, so rows of uneven
+// length and pairs beyond the cutoff leave fewer lanes idle through the
+// FP64 pair arithmetic.  For each item it forms the minimum-image gap h = |r| - (a_i + a_j) and
 // xi = 2h/(a_i + a_j) (Sec. II.B); pairs with xi > xi_max are skipped.  Each
 // remaining pair is oriented by tag (i = lower tag, n from i to j) and gets
 //   - lubrication, Eqs. 8, 13, 14, with resistances Eqs. 9-12, 15-18 at
@@ -15,9 +18,9 @@
 //     (k, tag_i, tag_j);
 //   - for h < 0 the contact force and torques, Eqs. 3-4, with tangential
 //     history (double, per list slot) and the Coulomb cap.
-// The sphere's own sums (with the one-body drag, Eqs. 5-6, and one-body
-// noise, Eqs. 20-21) stay in registers; the partner's share is added with
-// double atomics.  On sampled evaluations the pair virials F (x) r of the
+// Both spheres' shares, and each sphere's one-body drag (Eqs. 5-6) and
+// noise (Eqs. 20-21), are added with double atomics; the new contact bits of
+// a warp's spheres are gathered in shared memory.  On sampled evaluations the pair virials F (x) r of the
 // three components are reduced per block (Sec. II.A, II.B, II.D).
 // Optional terms: the short-range repulsion of Eq. 34 (read as the force on
 // j, so -(A/kappa) exp(-h/kappa) n on i) for h <= rep_cut kappa, with its
@@ -33,7 +36,7 @@
 namespace susp {
 
 template <bool NOISE, bool FRIC, bool SAMPLE>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, 2)
 k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
   __shared__ double smem[(kBlock / 32) * kPartialLen];
   const int b = blockIdx.x;
@@ -54,20 +57,28 @@ k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
   const int64_t t0 = RP.p0;
   const int64_t Np = A.Npad;
 
-  double vir[kPartialLen];
+  // pair virials of a sampled evaluation: each thread's own running sums in
+  // shared memory (entry e of thread t at sVir[e * kBlock + t]), which keeps
+  // them out of registers so that two blocks fit on an SM
+  extern __shared__ double sVir[];
+  if (SAMPLE) {
 #pragma unroll
-  for (int q = 0; q < kPartialLen; ++q) vir[q] = 0.0;
+    for (int q = 0; q < kPartialLen; ++q) sVir[q * kBlock + threadIdx.x] = 0.0;
+  }
 
+  const int tid = threadIdx.x, lane = tid & 31;
+  __shared__ unsigned long long sM[kBlock];  // new contact bits of the block's spheres
+  sM[tid] = 0ull;
+  int nn = 0;
   if (active) {
-    const double4_32a P = A.pos[cur][p];
-    const double4_32a VP = A.vel[cur][p];
-    const double4_32a WP = A.omg[cur][p];
-    const int tp = A.tag[cur][p];
-    const double ap = P.w;
-    double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
-
+    nn = A.nnb[cur][p];
     if (s.onebody) {
       // Eqs. 5-6 and 20-21
+      const double4_32a P = A.pos[cur][p];
+      const double4_32a VP = A.vel[cur][p];
+      const double4_32a WP = A.omg[cur][p];
+      const int tp = A.tag[cur][p];
+      const double ap = P.w;
       const double pi = 3.14159265358979323846;
       const double gt = 6.0 * pi * eta * ap;
       const double gr = 8.0 * pi * eta * ap * ap * ap;
@@ -76,23 +87,51 @@ k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
       double g[6] = {0, 0, 0, 0, 0, 0};
       if (NOISE) gauss6_f64(key0, key1, k, (uint32_t)(tp - t0), (uint32_t)(tp - t0), g);
       const double ct = c * sqrt(gt), cr = c * sqrt(gr);
-      F[0] += gt * (Uinf0 - VP.x) + (NOISE ? ct * g[0] : 0.0);
-      F[1] += gt * (0.0 - VP.y) + (NOISE ? ct * g[1] : 0.0);
-      F[2] += gt * (0.0 - VP.z) + (NOISE ? ct * g[2] : 0.0);
-      T[0] += gr * (0.0 - WP.x) + (NOISE ? cr * g[3] : 0.0);
-      T[1] += gr * (0.0 - WP.y) + (NOISE ? cr * g[4] : 0.0);
-      T[2] += gr * (Winf2 - WP.z) + (NOISE ? cr * g[5] : 0.0);
+      const double F[3] = {gt * (Uinf0 - VP.x) + (NOISE ? ct * g[0] : 0.0),
+                           gt * (0.0 - VP.y) + (NOISE ? ct * g[1] : 0.0),
+                           gt * (0.0 - VP.z) + (NOISE ? ct * g[2] : 0.0)};
+      const double T[3] = {gr * (0.0 - WP.x) + (NOISE ? cr * g[3] : 0.0),
+                           gr * (0.0 - WP.y) + (NOISE ? cr * g[4] : 0.0),
+                           gr * (Winf2 - WP.z) + (NOISE ? cr * g[5] : 0.0)};
+#pragma unroll
+      for (int q3 = 0; q3 < 3; ++q3) {
+        atomicAdd(A.frc[cur] + q3 * Np + p, F[q3]);
+        atomicAdd(A.trq[cur] + q3 * Np + p, T[q3]);
+      }
     }
-
-    const int nn = A.nnb[cur][p];
-    const int* __restrict__ row = A.nbr[cur] + p;
-    unsigned long long cm_old = 0ull, cm_new = 0ull;
-    if (FRIC) cm_old = A.cmsk[cur][p];
-    double* __restrict__ hist = FRIC ? A.hist[cur] : nullptr;
-    const int64_t hstride = (int64_t)A.kmax * Np;
-
-    for (int sl = 0; sl < nn; ++sl) {
-      const int q = row[(int64_t)sl * Np] & kNbrIndexMask;
+  }
+  // the warp's 32 rows flattened into one list of items: lane l takes items
+  // l, l + 32, ... whatever the rows' lengths
+  int incl = nn;
+#pragma unroll
+  for (int o2 = 1; o2 < 32; o2 <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o2);
+    if (lane >= o2) incl += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  const int excl = incl - nn;
+  double* __restrict__ hist = FRIC ? A.hist[cur] : nullptr;
+  const int64_t hstride = (int64_t)A.kmax * Np;
+  const int pw = bm.start[b] + (tid - lane);   // first sphere of the warp
+  __syncwarp();
+  for (int base = 0; base < total; base += 32) {
+    const int t = base + lane;
+    // owner row o of item t: the number of rows ending at or before t
+    int ow = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int v = __shfl_sync(0xffffffffu, incl, ow + step - 1);
+      if (v <= t) ow += step;
+    }
+    const int sl = t - __shfl_sync(0xffffffffu, excl, ow);
+    if (t < total) {
+      const int po = pw + ow;
+      const int q = A.nbr[cur][(int64_t)sl * Np + po] & kNbrIndexMask;
+      const double4_32a P = A.pos[cur][po];
+      const double4_32a VP = A.vel[cur][po];
+      const double4_32a WP = A.omg[cur][po];
+      const int tp = A.tag[cur][po];
+      const double ap = P.w;
       const double4_32a Q = A.pos[cur][q];
       double rpq[3], sy;
       min_image_f64(Q.x - P.x, Q.y - P.y, Q.z - P.z, L, iL, tilt, rpq, &sy);
@@ -106,7 +145,7 @@ k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
       const bool rep = s.rep_on && RP.rep_A > 0.0 && h <= s.rep_cut * kappa;
       const bool shp = SAMPLE && s.structural && h <= s.shell * ap;
       const bool shq = SAMPLE && s.structural && h <= s.shell * Q.w;
-      if (!lub && !rep && !shp && !shq) continue;
+      if (lub || rep || shp || shq) {
 
       const double4_32a VQ = A.vel[cur][q];
       const double4_32a WQ = A.omg[cur][q];
@@ -136,7 +175,7 @@ k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
 #pragma unroll
         for (int al = 0; al < 3; ++al)
 #pragma unroll
-          for (int be = 0; be < 3; ++be) vir[kStrOff + 3 * al + be] += w * n[al] * n[be];
+          for (int be = 0; be < 3; ++be) sVir[(kStrOff + 3 * al + be) * kBlock + tid] += w * n[al] * n[be];
       }
       double FR[3] = {0.0, 0.0, 0.0};
       if (rep) {
@@ -167,8 +206,8 @@ k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
         double Ft[3] = {0.0, 0.0, 0.0};
         if (FRIC && mu > 0.0) {
           double xt[3] = {0.0, 0.0, 0.0};
-          const int64_t hi = (int64_t)sl * Np + p;
-          if ((cm_old >> sl) & 1ull) {
+          const int64_t hi = (int64_t)sl * Np + po;
+          if ((A.cmsk[cur][po] >> sl) & 1ull) {
             xt[0] = hist[hi]; xt[1] = hist[hi + hstride]; xt[2] = hist[hi + 2 * hstride];
           }
           if (s.advance) {
@@ -180,7 +219,7 @@ k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
             history_update(xt, n, v, s.dt, kt, mu * kn * delta);
           }
           hist[hi] = xt[0]; hist[hi + hstride] = xt[1]; hist[hi + 2 * hstride] = xt[2];
-          cm_new |= 1ull << sl;
+          atomicOr(&sM[tid - lane + ow], 1ull << sl);
           Ft[0] = kt * xt[0]; Ft[1] = kt * xt[1]; Ft[2] = kt * xt[2];
         }
 #pragma unroll
@@ -202,52 +241,78 @@ k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
         Tj_[q3] = TCj[q3] + o.Tj[q3];
       }
       const int64_t qo = q;
-      if (p_is_i) {
+      const double sgn = p_is_i ? 1.0 : -1.0;
+      const double* To = p_is_i ? Ti_ : Tj_;
+      const double* Tq = p_is_i ? Tj_ : Ti_;
 #pragma unroll
-        for (int q3 = 0; q3 < 3; ++q3) {
-          F[q3] += Fi[q3];
-          T[q3] += Ti_[q3];
-          atomicAdd(A.frc[cur] + q3 * Np + qo, -Fi[q3]);
-          atomicAdd(A.trq[cur] + q3 * Np + qo, Tj_[q3]);
-        }
-      } else {
-#pragma unroll
-        for (int q3 = 0; q3 < 3; ++q3) {
-          F[q3] -= Fi[q3];
-          T[q3] += Tj_[q3];
-          atomicAdd(A.frc[cur] + q3 * Np + qo, Fi[q3]);
-          atomicAdd(A.trq[cur] + q3 * Np + qo, Ti_[q3]);
-        }
+      for (int q3 = 0; q3 < 3; ++q3) {
+        atomicAdd(A.frc[cur] + q3 * Np + po, sgn * Fi[q3]);
+        atomicAdd(A.trq[cur] + q3 * Np + po, To[q3]);
+        atomicAdd(A.frc[cur] + q3 * Np + qo, -sgn * Fi[q3]);
+        atomicAdd(A.trq[cur] + q3 * Np + qo, Tq[q3]);
       }
       if (SAMPLE) {
 #pragma unroll
         for (int al = 0; al < 3; ++al)
 #pragma unroll
           for (int be = 0; be < 3; ++be) {
-            vir[3 * al + be] += FC[al] * rr[be];
-            vir[9 + 3 * al + be] += o.FL[al] * rr[be];
-            vir[18 + 3 * al + be] += o.FB[al] * rr[be];
-            vir[kRepOff + 3 * al + be] += FR[al] * rr[be];
+            sVir[(3 * al + be) * kBlock + tid] += FC[al] * rr[be];
+            sVir[(9 + 3 * al + be) * kBlock + tid] += o.FL[al] * rr[be];
+            sVir[(18 + 3 * al + be) * kBlock + tid] += o.FB[al] * rr[be];
+            sVir[(kRepOff + 3 * al + be) * kBlock + tid] += FR[al] * rr[be];
           }
       }
-    }
-    if (FRIC) A.cmsk[cur][p] = cm_new;
-#pragma unroll
-    for (int q3 = 0; q3 < 3; ++q3) {
-      atomicAdd(A.frc[cur] + q3 * Np + p, F[q3]);
-      atomicAdd(A.trq[cur] + q3 * Np + p, T[q3]);
+      }
     }
   }
-  if (SAMPLE) block_sum_write<kPartialLen>(vir, smem, A.pair_partial + (int64_t)b * kPartialLen);
+  __syncwarp();
+  if (FRIC && active) A.cmsk[cur][p] = sM[tid];
+  if (SAMPLE) {
+    // the block's sums in a fixed order: a shuffle tree in each warp, then
+    // the warps in index order
+    const int warp = tid >> 5;
+    for (int c2 = 0; c2 < kPartialLen; ++c2) {
+      double x = sVir[c2 * kBlock + tid];
+#pragma unroll
+      for (int o2 = 16; o2 > 0; o2 >>= 1) x += __shfl_down_sync(0xffffffffu, x, o2);
+      if (lane == 0) smem[warp * kPartialLen + c2] = x;
+    }
+    __syncthreads();
+    for (int c2 = tid; c2 < kPartialLen; c2 += kBlock) {
+      double sum = 0.0;
+      for (int w2 = 0; w2 < kBlock / 32; ++w2) sum += smem[w2 * kPartialLen + c2];
+      A.pair_partial[(int64_t)b * kPartialLen + c2] = sum;
+    }
+  }
 }
+
+// dynamic shared memory of a sampled launch: the per-thread virial sums
+constexpr int kVirSmem = kPartialLen * kBlock * (int)sizeof(double);
 
 template <bool NOISE, bool FRIC>
 static void launch_sample(const Arrays& A, const BlockMap& bm, const StepArgs& s,
                           cudaStream_t st) {
   if (s.sample)
-    k_pair_fp64<NOISE, FRIC, true><<<bm.nblocks, kBlock, 0, st>>>(A, bm, s);
+    k_pair_fp64<NOISE, FRIC, true><<<bm.nblocks, kBlock, kVirSmem, st>>>(A, bm, s);
   else
     k_pair_fp64<NOISE, FRIC, false><<<bm.nblocks, kBlock, 0, st>>>(A, bm, s);
+}
+
+// The sampled launches use more dynamic shared memory than the 48 KB
+// default; the limit is raised per function on the current device (before
+// any stream capture: the handle's allocation calls this).
+int prepare_pair_fp64() {
+  cudaError_t e = cudaSuccess;
+  const auto raise = [&](const void* f) {
+    const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               kVirSmem);
+    if (r != cudaSuccess) e = r;
+  };
+  raise((const void*)k_pair_fp64<true, true, true>);
+  raise((const void*)k_pair_fp64<true, false, true>);
+  raise((const void*)k_pair_fp64<false, true, true>);
+  raise((const void*)k_pair_fp64<false, false, true>);
+  return e == cudaSuccess ? 0 : (int)e;
 }
 
 void launch_pair_fp64(const Arrays& A, const BlockMap& bm, const StepArgs& s,

@@ -263,6 +263,9 @@ void launch_finalize_fp64(const Arrays& A, const BlockMap& bm,
                           const StepArgs& s, int sample_kin, cudaStream_t st);
 void launch_pair_fp64(const Arrays& A, const BlockMap& bm, const StepArgs& s,
                       int tpp, cudaStream_t st);
+// raises the FP64 pair kernels' dynamic shared-memory limit on the current
+// device; 0 or the CUDA error code
+int prepare_pair_fp64();
 void launch_integrate_mixed(const Arrays& A, const BlockMap& bm,
                             const StepArgs& s, int close, int sample_kin,
                             cudaStream_t st, unsigned long long cond_handle,

@@ -185,9 +185,9 @@ def test_batch_of_the_replica_recipe_matches_the_oracle(precision, record):
     xb, Ub, _ = b.state()
     Fb, Tb = b.forces()
     off = np.concatenate([[0], np.cumsum([w.N for w in ws])])
-    # measured on a GB300: FP64 5.6e-13, mixed 1.6e-4 (the Pe = 0.1 replica,
+    # measured on a GB300: FP64 2.2e-12, mixed 1.6e-4 (the Pe = 0.1 replica,
     # noise through single-precision Box-Muller, grown over 100 steps)
-    tol_f = 1e-11 if precision == "fp64" else 1e-3
+    tol_f = 3e-11 if precision == "fp64" else 1e-3
     worst = 0.0
     for r, (w, (xo, Uo, Fo, To, so)) in enumerate(zip(ws, ref)):
         sl = slice(off[r], off[r + 1])
