@@ -48,8 +48,8 @@ NCU_TRAFFIC = {
     # ncu --set full on the 1M bench workload: DRAM read + write per launch / N
     # issue_active: fraction of cycles the kernel issued an instruction (the
     # pair kernel is bound by issue and latency, not by DRAM)
-    "k_pair_mixed": {"bytes_per_sphere": 316.797, "source_sha": "34e9ae9eab9a9df3",
-                     "issue_active": 0.761, "dram_throughput": 0.211},
+    "k_pair_mixed": {"bytes_per_sphere": 316.836, "source_sha": "10e1737ecc9446df",
+                     "issue_active": 0.762, "dram_throughput": 0.216},
     "k_integrate_mixed": {"bytes_per_sphere": 265.448, "source_sha": "642ebccc2ca93352"},
 }
 
