@@ -14,7 +14,9 @@
 //          the pair kernel rebuilds separations and the gap
 //          h = (d^2 - S^2)/(d + S) to ~1e-12 for any box size;
 //   velm = (U - U_inf(y), tag): velocity relative to the imposed flow;
-//   omgm = (Omega, home cell coordinates packed 10 bits per axis).
+//   omgm = (Omega, home cell coordinates packed 10 bits per axis; the pair
+//          kernel takes cell offsets from the list entries instead, so the
+//          packed cell only labels the record).
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
