@@ -106,10 +106,15 @@ typedef struct susp_params {
   double rep_cut;     /* repulsion acts for h <= rep_cut kappa,             */
                       /* kappa = 0.01 (a_i + a_j) (default 10)              */
   double shell;       /* structural shell Delta / a_i (paper: 0.05)         */
-  int32_t deterministic; /* must be 0: force sums use atomics, so their     */
-                      /* order (and the last bits) may change from run to   */
-                      /* run; the stress reductions are always in a fixed   */
-                      /* order                                              */
+  int32_t deterministic; /* 0: force sums use atomics, so their order (and */
+                      /* the last bits) may change from run to run; 1      */
+                      /* (SUSP_FP64 only, kmax * N < 2^31): each pair's     */
+                      /* shares go to its own slot and every sphere sums    */
+                      /* them in a fixed order, so repeated runs are        */
+                      /* bitwise equal (a step costs about 3% more at 1M    */
+                      /* spheres; the reverse list takes 4 B per slot and  */
+                      /* the shares 72 B per slot).                         */
+                      /* The stress reductions are always in a fixed order  */
   int32_t autotune;   /* 1: the first step call of the handle runs          */
                       /* susp_autotune() over the skins 0.2, 0.3, 0.45,    */
                       /* 0.6 and 0.8 (100 trial steps each) and keeps the  */

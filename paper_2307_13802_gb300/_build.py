@@ -32,6 +32,7 @@ UNITS = [
     ("k_mixed.cu", ["-fmad=true"]),
     ("k_pair_mixed.cu", ["-fmad=true", "-prec-div=false", "-prec-sqrt=false"]),
     ("noalloc.cu", ["-fmad=false"]),
+    ("k_det.cu", ["-fmad=false"]),
 ]
 
 

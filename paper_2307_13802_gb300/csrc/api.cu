@@ -150,9 +150,12 @@ int validate_params(const susp_params* p, std::string& msg) {
   if (p->series_cap < 0) { msg = "series_cap must be >= 0"; return SUSP_EINVAL; }
   if (p->series_cap > 0 && !p->structural) { msg = "series_cap needs structural = 1"; return SUSP_EINVAL; }
   if (p->rebuild_every < 0) { msg = "rebuild_every must be >= 0"; return SUSP_EINVAL; }
-  if (p->deterministic != 0) {
-    msg = "deterministic = 1 is not offered: the force sums use atomics (the stress "
-          "reductions are in a fixed order)";
+  if (p->deterministic != 0 && p->deterministic != 1) {
+    msg = "deterministic must be 0 or 1"; return SUSP_EINVAL;
+  }
+  if (p->deterministic && p->precision != SUSP_FP64) {
+    msg = "deterministic = 1 needs precision SUSP_FP64 (the mixed path's force sums use "
+          "atomics)";
     return SUSP_EINVAL;
   }
   if (p->autotune != 0 && p->autotune != 1) { msg = "autotune must be 0 or 1"; return SUSP_EINVAL; }
@@ -182,6 +185,12 @@ int common_create(susp_t** out, int32_t R, const int64_t* N_r,
   int64_t N = 0;
   for (int r = 0; r < R; ++r) N += N_r[r];
   if (N >= (int64_t)1 << 31) { g_create_error = "too many spheres"; return SUSP_EINVAL; }
+  if (p_r[0].deterministic &&
+      (int64_t)(p_r[0].kmax > 0 ? p_r[0].kmax : 48) * ((N + 31) / 32 * 32) >= (int64_t)1 << 31) {
+    // the reverse list of the deterministic sums holds 32-bit slot indices
+    g_create_error = "deterministic = 1 needs kmax * N below 2^31";
+    return SUSP_EINVAL;
+  }
   if (p_r[0].precision == SUSP_MIXED && N > kNbrIndexMask) {
     // list entries keep the partner's home-cell offset in their top bits
     g_create_error = "the mixed path holds at most 134,217,727 spheres";
@@ -393,6 +402,19 @@ int allocate(susp_t* h) {
   ok &= alloc_n(h, &A.rep_tk, h->R);
   ok &= alloc_n(h, &A.repl, h->R);
   ok &= alloc_n(h, &A.ctl, 1);
+  A.det = h->p0.deterministic;
+  if (A.det) {
+    // per-slot pair shares [9][kmax][Npad], one-body terms [6][Npad], the
+    // reverse list (offsets, entries) and its scan's block totals
+    const int64_t KN = (int64_t)h->kmax * Np;
+    ok &= alloc_n(h, &A.det_slot, 9 * KN);
+    ok &= alloc_n(h, &A.det_own, 6 * Np);
+    ok &= alloc_n(h, &A.rev_cnt, h->N + 1);
+    ok &= alloc_n(h, &A.rev_fill, h->N + 1);
+    ok &= alloc_n(h, &A.rev_off, h->N + 1);
+    ok &= alloc_n(h, &A.rev_ent, KN);
+    ok &= alloc_n(h, &A.rev_part, (h->N + kBlock * 8 - 1) / (kBlock * 8) + 1);
+  }
   if (h->p0.precision == SUSP_MIXED) {
     ok &= alloc_n(h, &A.posm, 2 * Np);  // 32-byte (hi, lo) records
     ok &= alloc_n(h, &A.velm, Np);
@@ -598,7 +620,8 @@ void launch_reduce(susp_t* h, int sample_pair, int sample_kin, int ppar, cudaStr
 
 // kernels in one neighbour rebuild (gated sequence of k_neighbors.cu)
 int rebuild_kernels(const susp_t* h, const StepArgs& s) {
-  return 11 + (s.friction ? 1 : 0) + (h->p0.precision == SUSP_MIXED ? 1 : 0);
+  return 11 + (s.friction ? 1 : 0) + (h->p0.precision == SUSP_MIXED ? 1 : 0) +
+         (h->A.det ? 7 : 0);
 }
 
 // Setup evaluation (time not advanced): rebuild if due, clear, evaluate.
@@ -681,9 +704,10 @@ void enqueue_steps(susp_t* h, int64_t first, int64_t n, double dt,
     }
     launch_pair(h, s, st);
     if (!fused) launch_reduce(h, samp, skin_prev, 0, st);
-    // integrator + pair kernel, and the two reduction kernels when sampling
+    // integrator + pair kernel (and the deterministic gather), and the two
+    // reduction kernels when sampling
     (capture ? h->capture_launches : h->launches) +=
-        2 + ((!fused && (samp || skin_prev)) ? 2 : 0);
+        2 + (h->A.det ? 1 : 0) + ((!fused && (samp || skin_prev)) ? 2 : 0);
   }
   StepArgs s = make_args(h, dt, 1, 0);
   const int last_kin = sampled(h, first + n - 1);

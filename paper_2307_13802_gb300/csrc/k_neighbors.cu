@@ -441,6 +441,7 @@ void launch_rebuild(const Arrays& A, const BlockMap& bm, const StepArgs& s,
   k_build_list<<<grid_for(A.N), kBlock, 0, st>>>(A, s, 1.0 + 0.5 * s.xi_max);
   if (s.friction) k_remap_history<<<grid_for(A.N), kBlock, 0, st>>>(A);
   if (mixed) launch_mirror_gated_next(A, st);
+  if (A.det) launch_rev_build(A, st);
   k_finish<<<1, 1, 0, st>>>(A);
 }
 

@@ -35,7 +35,9 @@
 
 namespace susp {
 
-template <bool NOISE, bool FRIC, bool SAMPLE>
+// DET: the shares go to per-slot and per-sphere records that k_det_gather
+// sums in a fixed order, instead of double atomics
+template <bool NOISE, bool FRIC, bool SAMPLE, bool DET>
 __global__ void __launch_bounds__(kBlock, 2)
 k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
   __shared__ double smem[(kBlock / 32) * kPartialLen];
@@ -95,9 +97,17 @@ k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
                            gr * (Winf2 - WP.z) + (NOISE ? cr * g[5] : 0.0)};
 #pragma unroll
       for (int q3 = 0; q3 < 3; ++q3) {
-        atomicAdd(A.frc[cur] + q3 * Np + p, F[q3]);
-        atomicAdd(A.trq[cur] + q3 * Np + p, T[q3]);
+        if (DET) {
+          A.det_own[q3 * Np + p] = F[q3];
+          A.det_own[(3 + q3) * Np + p] = T[q3];
+        } else {
+          atomicAdd(A.frc[cur] + q3 * Np + p, F[q3]);
+          atomicAdd(A.trq[cur] + q3 * Np + p, T[q3]);
+        }
       }
+    } else if (DET) {
+#pragma unroll
+      for (int c6 = 0; c6 < 6; ++c6) A.det_own[c6 * Np + p] = 0.0;
     }
   }
   // the warp's 32 rows flattened into one list of items: lane l takes items
@@ -244,12 +254,22 @@ k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
       const double sgn = p_is_i ? 1.0 : -1.0;
       const double* To = p_is_i ? Ti_ : Tj_;
       const double* Tq = p_is_i ? Tj_ : Ti_;
+      if (DET) {
+        const int64_t e = (int64_t)sl * Np + po, KN = (int64_t)A.kmax * Np;
 #pragma unroll
-      for (int q3 = 0; q3 < 3; ++q3) {
-        atomicAdd(A.frc[cur] + q3 * Np + po, sgn * Fi[q3]);
-        atomicAdd(A.trq[cur] + q3 * Np + po, To[q3]);
-        atomicAdd(A.frc[cur] + q3 * Np + qo, -sgn * Fi[q3]);
-        atomicAdd(A.trq[cur] + q3 * Np + qo, Tq[q3]);
+        for (int q3 = 0; q3 < 3; ++q3) {
+          A.det_slot[q3 * KN + e] = sgn * Fi[q3];
+          A.det_slot[(3 + q3) * KN + e] = To[q3];
+          A.det_slot[(6 + q3) * KN + e] = Tq[q3];
+        }
+      } else {
+#pragma unroll
+        for (int q3 = 0; q3 < 3; ++q3) {
+          atomicAdd(A.frc[cur] + q3 * Np + po, sgn * Fi[q3]);
+          atomicAdd(A.trq[cur] + q3 * Np + po, To[q3]);
+          atomicAdd(A.frc[cur] + q3 * Np + qo, -sgn * Fi[q3]);
+          atomicAdd(A.trq[cur] + q3 * Np + qo, Tq[q3]);
+        }
       }
       if (SAMPLE) {
 #pragma unroll
@@ -262,6 +282,11 @@ k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
             sVir[(kRepOff + 3 * al + be) * kBlock + tid] += FR[al] * rr[be];
           }
       }
+      } else if (DET) {
+        // a listed pair that does not interact: its slot holds zeros
+        const int64_t e = (int64_t)sl * Np + po, KN = (int64_t)A.kmax * Np;
+#pragma unroll
+        for (int c9 = 0; c9 < 9; ++c9) A.det_slot[c9 * KN + e] = 0.0;
       }
     }
   }
@@ -289,13 +314,24 @@ k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
 // dynamic shared memory of a sampled launch: the per-thread virial sums
 constexpr int kVirSmem = kPartialLen * kBlock * (int)sizeof(double);
 
-template <bool NOISE, bool FRIC>
+template <bool NOISE, bool FRIC, bool DET>
 static void launch_sample(const Arrays& A, const BlockMap& bm, const StepArgs& s,
                           cudaStream_t st) {
   if (s.sample)
-    k_pair_fp64<NOISE, FRIC, true><<<bm.nblocks, kBlock, kVirSmem, st>>>(A, bm, s);
+    k_pair_fp64<NOISE, FRIC, true, DET><<<bm.nblocks, kBlock, kVirSmem, st>>>(A, bm, s);
   else
-    k_pair_fp64<NOISE, FRIC, false><<<bm.nblocks, kBlock, 0, st>>>(A, bm, s);
+    k_pair_fp64<NOISE, FRIC, false, DET><<<bm.nblocks, kBlock, 0, st>>>(A, bm, s);
+}
+
+template <bool DET>
+static void launch_det(const Arrays& A, const BlockMap& bm, const StepArgs& s,
+                       cudaStream_t st) {
+  const bool noise = s.noise != 0;
+  const bool fric = s.friction != 0;
+  if (noise && fric) launch_sample<true, true, DET>(A, bm, s, st);
+  else if (noise) launch_sample<true, false, DET>(A, bm, s, st);
+  else if (fric) launch_sample<false, true, DET>(A, bm, s, st);
+  else launch_sample<false, false, DET>(A, bm, s, st);
 }
 
 // The sampled launches use more dynamic shared memory than the 48 KB
@@ -308,22 +344,26 @@ int prepare_pair_fp64() {
                                                kVirSmem);
     if (r != cudaSuccess) e = r;
   };
-  raise((const void*)k_pair_fp64<true, true, true>);
-  raise((const void*)k_pair_fp64<true, false, true>);
-  raise((const void*)k_pair_fp64<false, true, true>);
-  raise((const void*)k_pair_fp64<false, false, true>);
+  raise((const void*)k_pair_fp64<true, true, true, false>);
+  raise((const void*)k_pair_fp64<true, false, true, false>);
+  raise((const void*)k_pair_fp64<false, true, true, false>);
+  raise((const void*)k_pair_fp64<false, false, true, false>);
+  raise((const void*)k_pair_fp64<true, true, true, true>);
+  raise((const void*)k_pair_fp64<true, false, true, true>);
+  raise((const void*)k_pair_fp64<false, true, true, true>);
+  raise((const void*)k_pair_fp64<false, false, true, true>);
   return e == cudaSuccess ? 0 : (int)e;
 }
 
 void launch_pair_fp64(const Arrays& A, const BlockMap& bm, const StepArgs& s,
                       int tpp, cudaStream_t st) {
   (void)tpp;
-  const bool noise = s.noise != 0;
-  const bool fric = s.friction != 0;
-  if (noise && fric) launch_sample<true, true>(A, bm, s, st);
-  else if (noise) launch_sample<true, false>(A, bm, s, st);
-  else if (fric) launch_sample<false, true>(A, bm, s, st);
-  else launch_sample<false, false>(A, bm, s, st);
+  if (A.det) {
+    launch_det<true>(A, bm, s, st);
+    launch_det_gather(A, st);
+  } else {
+    launch_det<false>(A, bm, s, st);
+  }
 }
 
 }  // namespace susp

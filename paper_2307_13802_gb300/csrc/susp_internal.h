@@ -187,6 +187,16 @@ struct Arrays {
   Pair2<double> hist;
   Pair2<unsigned long long> cmsk;
   int* slot_of_tag;     // tag -> sorted index (live copy)
+  // deterministic force sums (FP64 path, deterministic = 1)
+  int det;              // 1: pair shares go to per-slot records
+  double* det_slot;     // [9][kmax * Npad]: force and torque on the row's
+                        // sphere, torque on the partner
+  double* det_own;      // [6][Npad]: one-body force and torque
+  int* rev_cnt;         // [N + 1] times each sphere is a partner
+  int* rev_fill;        // [N + 1] fill counters
+  int* rev_off;         // [N + 1] offsets into rev_ent
+  int* rev_ent;         // [kmax * Npad] slots (sl * Npad + p) of each partner
+  int* rev_part;        // scan block totals
   int* cell;            // home cell of sorted particle (new order after build)
   float4* posm;         // mixed-precision mirrors
   float4* velm;
@@ -266,6 +276,10 @@ void launch_pair_fp64(const Arrays& A, const BlockMap& bm, const StepArgs& s,
 // raises the FP64 pair kernels' dynamic shared-memory limit on the current
 // device; 0 or the CUDA error code
 int prepare_pair_fp64();
+// deterministic sums (k_det.cu): the reverse list (gated, in the rebuild)
+// and the per-sphere gather after the pair kernel
+void launch_rev_build(const Arrays& A, cudaStream_t st);
+void launch_det_gather(const Arrays& A, cudaStream_t st);
 void launch_integrate_mixed(const Arrays& A, const BlockMap& bm,
                             const StepArgs& s, int close, int sample_kin,
                             cudaStream_t st, unsigned long long cond_handle,

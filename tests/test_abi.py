@@ -98,7 +98,8 @@ def test_parameters_are_checked_before_any_device_work():
     # invalid parameters are reported as SUSP_EINVAL with or without a GPU
     import paper_2307_13802_gb300 as s
 
-    for bad in (dict(deterministic=1), dict(rebuild_every=-1), dict(autotune=2),
+    for bad in (dict(deterministic=1, precision="mixed"), dict(deterministic=2),
+                dict(rebuild_every=-1), dict(autotune=2),
                 dict(sample_every=0), dict(xi_min=0.1, xi_max=0.05)):
         try:
             s.System([1.0] * 10, [30.0, 30.0, 30.0], **bad)

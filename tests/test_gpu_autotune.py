@@ -104,3 +104,49 @@ def test_rebuild_every_and_autotune_parameters(record):
         record(f"{name}_force", _relerr(F, F0), 1e-9)
         assert _relerr(F, F0) <= 1e-9, name
         assert info["k"] == i0["k"] and s["samples"] == s0["samples"] == 200
+
+
+def test_tuned_batch_is_not_slower_than_the_default_skin(record):
+    # a mixed batch of uneven replicas (Pe 0.2 to 500, phi 0.45 to 0.58,
+    # friction 0 to 1): the autotuner's pick runs at least as fast as the
+    # default skin 0.3, in its own trials and in a separate timed run after
+    # it (CUDA events; 5% for the timing noise of a shared GPU)
+    import time
+
+    import paper_2307_13802_gb300 as susp
+
+    rows = [(3000, 0.45, 0.2, 0.0), (5000, 0.55, 5.0, 1.0), (4000, 0.58, 500.0, 0.5),
+            (2500, 0.50, 50.0, 1.0)]
+    ws = [workloads.make(n, phi, pe, mu, pack_seed=900 + i, dyn_seed=910 + i, tol=1e-2)
+          for i, (n, phi, pe, mu) in enumerate(rows)]
+    kw = [_args(w, "mixed") for w in ws]
+    dt = ws[0].params["dt"]
+
+    def make():
+        b = susp.System.batch([w.N for w in ws], np.concatenate([w.radii for w in ws]),
+                              np.stack([w.box for w in ws]), kw)
+        b.set_state(np.concatenate([w.x for w in ws]), np.concatenate([w.U for w in ws]),
+                    np.concatenate([w.W for w in ws]))
+        b.step_batch(200, dt)
+        return b
+
+    skins = [0.1, 0.3, 0.6, 1.0]
+    b = make()
+    chosen, ms = b.autotune(300, dt, skins)
+    record("trial_ratio_chosen_over_default", ms[skins.index(chosen)] / ms[1], 1.0)
+    assert ms[skins.index(chosen)] <= ms[1]
+
+    def timed(skin):
+        g = make()
+        g.set_skin(skin)
+        g.step_batch(64, dt)           # capture the graphs
+        prof = g.profile(1, dt)        # synchronises
+        del prof
+        t0 = time.perf_counter()
+        g.step_batch(640, dt)
+        g.info()                        # synchronises through a device read
+        return time.perf_counter() - t0
+
+    t_default, t_tuned = timed(0.3), timed(chosen)
+    record("run_ratio_tuned_over_default", t_tuned / t_default, 1.05)
+    assert t_tuned <= 1.05 * t_default, (chosen, t_tuned, t_default)
