@@ -124,6 +124,26 @@ __device__ __forceinline__ void df_diff_shift(float qh, float ql, float ph, floa
   fast_two_sum(s2, lo, rh, rl);
 }
 
+// Packed single-precision pairs (two lanes of one FP32 instruction on
+// sm_100 and later), used where the operands come in natural pairs: the x
+// and y components of the gap, and the (x, y) rows of the virial products.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = add2(a, b);
+  const float2 bb = sub2(s, a);
+  e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = add2(a, b);
+  e = sub2(b, sub2(s, a));
+}
+
+__device__ __forceinline__ float2 dup2(float s) { return make_float2(s, s); }
+
 // Sums v[0..31] over the 32 lanes of a warp and leaves the total of
 // component l in lane l: five halving stages, in each of which a lane keeps
 // one half of its components and adds the partner's copy of that half
@@ -381,13 +401,15 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
     red_add_v4(T4 + q, Tq[0], Tq[1], Tq[2], 0.f);
     if (SAMPLE) {
 #pragma unroll
-      for (int al = 0; al < 3; ++al)
-#pragma unroll
-        for (int be = 0; be < 3; ++be) {
-          vp[3 * al + be] = FC[al] * rr[be];
-          vp[9 + 3 * al + be] = ou.FL[al] * rr[be];
-          vp[18 + 3 * al + be] = ou.FB[al] * rr[be];
-        }
+      for (int be = 0; be < 3; ++be) {
+        const float2 rb = dup2(rr[be]);
+        const float2 c2 = mul2(make_float2(FC[0], FC[1]), rb);
+        const float2 l2 = mul2(make_float2(ou.FL[0], ou.FL[1]), rb);
+        const float2 b2 = mul2(make_float2(ou.FB[0], ou.FB[1]), rb);
+        vp[be] = c2.x; vp[3 + be] = c2.y; vp[6 + be] = FC[2] * rr[be];
+        vp[9 + be] = l2.x; vp[12 + be] = l2.y; vp[15 + be] = ou.FL[2] * rr[be];
+        vp[18 + be] = b2.x; vp[21 + be] = b2.y; vp[24 + be] = ou.FB[2] * rr[be];
+      }
     }
     return o;
   };
@@ -521,8 +543,16 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
           const float2 shx = sShx[c9];
           const float fy = (float)dcy, fz = (float)dcz;
           float rh[3], rl[3];
-          df_diff_shift(Q.x, Ql.x, P.x, Pl.x, shx.x, shx.y, rh[0], rl[0]);
-          df_diff_shift(Q.y, Ql.y, P.y, Pl.y, cw1h * fy, cw1l * fy, rh[1], rl[1]);
+          {
+            // x and y as packed pairs, z alone
+            float2 s1, e1, s2, e2, h2, l2;
+            two_sum2(make_float2(Q.x, Q.y), make_float2(-P.x, -P.y), s1, e1);
+            two_sum2(s1, make_float2(shx.x, cw1h * fy), s2, e2);
+            const float2 dl = sub2(make_float2(Ql.x, Ql.y), make_float2(Pl.x, Pl.y));
+            const float2 lo = add2(add2(e1, e2), add2(dl, make_float2(shx.y, cw1l * fy)));
+            fast_two_sum2(s2, lo, h2, l2);
+            rh[0] = h2.x; rh[1] = h2.y; rl[0] = l2.x; rl[1] = l2.y;
+          }
           df_diff_shift(Q.z, Ql.z, P.z, Pl.z, cw2h * fz, cw2l * fz, rh[2], rl[2]);
           float Sh, Sl;
           {
@@ -531,10 +561,13 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
             fast_two_sum(s0, __fadd_rn(e0, __fadd_rn(Pl.w, Ql.w)), Sh, Sl);
           }
           float pk[3], ek[3];
-#pragma unroll
-          for (int k3 = 0; k3 < 3; ++k3) {
-            pk[k3] = __fmul_rn(rh[k3], rh[k3]);
-            ek[k3] = __fmaf_rn(rh[k3], rh[k3], -pk[k3]);
+          {
+            const float2 r2 = make_float2(rh[0], rh[1]);
+            const float2 p2 = mul2(r2, r2);
+            const float2 e2 = fma2(r2, r2, neg2(p2));
+            pk[0] = p2.x; pk[1] = p2.y; ek[0] = e2.x; ek[1] = e2.y;
+            pk[2] = __fmul_rn(rh[2], rh[2]);
+            ek[2] = __fmaf_rn(rh[2], rh[2], -pk[2]);
           }
           const float pS = __fmul_rn(Sh, Sh);
           const float eS = __fmaf_rn(Sh, Sh, -pS);
