@@ -175,10 +175,15 @@ k_integrate_mixed(Arrays A, BlockMap bm, StepArgs s, int close, int sample_kin,
     load_df3(A.pos[cur], p, x, a, &alo);
     load_df3(A.vel[cur], p, U, im);
     load_df3(A.omg[cur], p, W, iI);
+    cellkey = A.cell[p];
+    tagp = A.tag[cur][p];
+  }
+  // the state above is not written by the pair kernel; the forces are, and
+  // the mirrors written below are read by it: wait for that grid here
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (active) {
     f = F4[p];
     t = T4[p];
-    cellkey = A.cell[p];     // issued with the other loads
-    tagp = A.tag[cur][p];
   }
   const float cm = hdt * im, cI = hdt * iI;
   if (close) {
@@ -407,8 +412,20 @@ void launch_integrate_mixed(const Arrays& A, const BlockMap& bm, const StepArgs&
                             unsigned long long cond_handle, int use_cond) {
   float dth, dtl;
   split_df(s.dt, dth, dtl);
-  k_integrate_mixed<<<bm.nblocks, kBlock, 0, st>>>(A, bm, s, close, sample_kin, cond_handle,
-                                                   use_cond, dth, dtl, (float)s.hdt);
+  // programmatic dependent launch: the blocks may become resident during the
+  // pair kernel's last wave and load their state before it ends
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)bm.nblocks);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_integrate_mixed, A, bm, s, close, sample_kin, cond_handle, use_cond,
+                     dth, dtl, (float)s.hdt);
 }
 
 void launch_finalize_mixed(const Arrays& A, const BlockMap& bm, const StepArgs& s,

@@ -183,6 +183,9 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   __shared__ float sA[kBlock];  // radius (high word) of each owner sphere
   __shared__ int sArrive;
   const int b = blockIdx.x;
+  // the integrator that follows may start its blocks (which wait for this
+  // grid before reading forces) once every block of this grid has started
+  asm volatile("griddepcontrol.launch_dependents;");
   // the previous sampled step's stress: block ch < nchunk reduces chunk ch
   // of it before its own spheres, and the last chunk of a replica sums the
   // replica (its pair partials are in the other buffer)
