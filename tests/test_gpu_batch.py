@@ -6,10 +6,13 @@ The replicas share kernels and launches but no data: each has its own box,
 cell grid, strain, noise key and stress sums, and its particles are never
 paired with another replica's.  The per-replica results therefore equal
 those of separate handles up to the order of the force sums (atomics), the
-same bar as two runs of one handle.  Bars are 10-30 times the largest
-difference measured on a GB300 over 200 steps: FP64 x 8e-15, U 1.4e-13,
-F 2.4e-13; mixed (single-precision force atomics) x 2.5e-8, U 2.5e-7,
-F 8e-7 of the largest entry."""
+same bar as two runs of one handle.  Bars are about 10 times the largest
+difference measured on a GB300 over 200 steps (seven runs): FP64 x 8e-15,
+U 1.4e-13, F 4.4e-13; mixed (single-precision force atomics) x 4.5e-8,
+U 1.2e-6, F 4.5e-6 of the largest entry.  The mixed maxima are heavy-tailed
+from run to run (1.6e-7 to 4.5e-6 in F): the noisiest replica (Pe 0.5)
+amplifies a different order of the float atomics, and a pair that enters
+the cutoff or touches one step apart moves the largest force entry."""
 import numpy as np
 import pytest
 
@@ -21,7 +24,7 @@ ROWS = [dict(N=300, phi=0.45, pe=1000.0, mu=0.0, seed=71),
         dict(N=520, phi=0.55, pe=10.0, mu=1.0, seed=72),
         dict(N=410, phi=0.50, pe=0.5, mu=0.5, seed=73)]
 # (x absolute, U relative to its largest entry, F normwise)
-TOL = {"fp64": (1e-13, 3e-12, 5e-12), "mixed": (5e-7, 5e-6, 1e-5)}
+TOL = {"fp64": (1e-13, 3e-12, 5e-12), "mixed": (5e-7, 1e-5, 5e-5)}
 
 
 def _kw(w, precision):
