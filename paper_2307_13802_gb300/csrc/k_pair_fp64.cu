@@ -7,11 +7,15 @@
 // pipe, from 21 to 10 per lubricated pair.
 //
 // Each warp owns 32 spheres of the sorted order and flattens their half-list
-// rows into one list of items, one item per lane per pass, so rows of uneven
-// length and pairs beyond the cutoff leave fewer lanes idle through the
-// FP64 pair arithmetic.  For each item it forms the minimum-image gap h = |r| - (a_i + a_j) and
-// xi = 2h/(a_i + a_j) (Sec. II.B); pairs with xi > xi_max are skipped.  Each
-// remaining pair is oriented by tag (i = lower tag, n from i to j) and gets
+// rows into one list of items.  A pass tests 32 items against the widest
+// interaction range and queues those within it in shared memory, touching
+// pairs apart from the others; the pair arithmetic then runs on full
+// batches of 32 queued pairs, so rows of uneven length, pairs beyond the
+// cutoff and the contact branch leave no lanes idle through the FP64
+// arithmetic.  For each pair it forms the minimum-image gap
+// h = |r| - (a_i + a_j) and xi = 2h/(a_i + a_j) (Sec. II.B); pairs with
+// xi > xi_max are skipped.  Each remaining pair is oriented by tag
+// (i = lower tag, n from i to j) and gets
 //   - lubrication, Eqs. 8, 13, 14, with resistances Eqs. 9-12, 15-18 at
 //     xi_eff = max(xi, xi_min);
 //   - pair Brownian force and torques, Eqs. 22-24, Philox counter
@@ -124,171 +128,252 @@ k_pair_fp64(Arrays A, BlockMap bm, StepArgs s) {
   const int64_t hstride = (int64_t)A.kmax * Np;
   const int pw = bm.start[b] + (tid - lane);   // first sphere of the warp
   __syncwarp();
-  for (int base = 0; base < total; base += 32) {
-    const int t = base + lane;
-    // owner row o of item t: the number of rows ending at or before t
-    int ow = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-      const int v = __shfl_sync(0xffffffffu, incl, ow + step - 1);
-      if (v <= t) ow += step;
+  // One listed pair (owner row ow of the warp, slot sl): the exact range
+  // tests, then the pair's physics.  It has a single call site, in the
+  // batch step of the work loop below.
+  auto item = [&](int ow, int sl) {
+    const int po = pw + ow;
+    const int q = A.nbr[cur][(int64_t)sl * Np + po] & kNbrIndexMask;
+    const double4_32a P = A.pos[cur][po];
+    const double4_32a VP = A.vel[cur][po];
+    const double4_32a WP = A.omg[cur][po];
+    const int tp = A.tag[cur][po];
+    const double ap = P.w;
+    const double4_32a Q = A.pos[cur][q];
+    double rpq[3], sy;
+    min_image_f64(Q.x - P.x, Q.y - P.y, Q.z - P.z, L, iL, tilt, rpq, &sy);
+    const double d2 = rpq[0] * rpq[0] + rpq[1] * rpq[1] + rpq[2] * rpq[2];
+    const double d = sqrt(d2);
+    const double S = ap + Q.w;
+    const double h = d - S;
+    const double xi = 2.0 * h / S;
+    const double kappa = 0.01 * S;
+    const bool lub = xi <= s.xi_max;
+    const bool rep = s.rep_on && RP.rep_A > 0.0 && h <= s.rep_cut * kappa;
+    const bool shp = SAMPLE && s.structural && h <= s.shell * ap;
+    const bool shq = SAMPLE && s.structural && h <= s.shell * Q.w;
+    if (lub || rep || shp || shq) {
+
+    const double4_32a VQ = A.vel[cur][q];
+    const double4_32a WQ = A.omg[cur][q];
+    const int tq = A.tag[cur][q];
+    const bool p_is_i = tp < tq;
+    // orient: i = lower tag, n and r from i to j
+    double rr[3], syij, ai, aj;
+    double Ui[3], Uj[3], Wi[3], Wj[3];
+    if (p_is_i) {
+      rr[0] = rpq[0]; rr[1] = rpq[1]; rr[2] = rpq[2]; syij = sy;
+      ai = ap; aj = Q.w;
+      Ui[0] = VP.x; Ui[1] = VP.y; Ui[2] = VP.z; Uj[0] = VQ.x; Uj[1] = VQ.y; Uj[2] = VQ.z;
+      Wi[0] = WP.x; Wi[1] = WP.y; Wi[2] = WP.z; Wj[0] = WQ.x; Wj[1] = WQ.y; Wj[2] = WQ.z;
+    } else {
+      rr[0] = -rpq[0]; rr[1] = -rpq[1]; rr[2] = -rpq[2]; syij = -sy;
+      ai = Q.w; aj = ap;
+      Ui[0] = VQ.x; Ui[1] = VQ.y; Ui[2] = VQ.z; Uj[0] = VP.x; Uj[1] = VP.y; Uj[2] = VP.z;
+      Wi[0] = WQ.x; Wi[1] = WQ.y; Wi[2] = WQ.z; Wj[0] = WP.x; Wj[1] = WP.y; Wj[2] = WP.z;
     }
-    const int sl = t - __shfl_sync(0xffffffffu, excl, ow);
-    if (t < total) {
-      const int po = pw + ow;
-      const int q = A.nbr[cur][(int64_t)sl * Np + po] & kNbrIndexMask;
-      const double4_32a P = A.pos[cur][po];
-      const double4_32a VP = A.vel[cur][po];
-      const double4_32a WP = A.omg[cur][po];
-      const int tp = A.tag[cur][po];
-      const double ap = P.w;
-      const double4_32a Q = A.pos[cur][q];
-      double rpq[3], sy;
-      min_image_f64(Q.x - P.x, Q.y - P.y, Q.z - P.z, L, iL, tilt, rpq, &sy);
-      const double d2 = rpq[0] * rpq[0] + rpq[1] * rpq[1] + rpq[2] * rpq[2];
-      const double d = sqrt(d2);
-      const double S = ap + Q.w;
-      const double h = d - S;
-      const double xi = 2.0 * h / S;
-      const double kappa = 0.01 * S;
-      const bool lub = xi <= s.xi_max;
-      const bool rep = s.rep_on && RP.rep_A > 0.0 && h <= s.rep_cut * kappa;
-      const bool shp = SAMPLE && s.structural && h <= s.shell * ap;
-      const bool shq = SAMPLE && s.structural && h <= s.shell * Q.w;
-      if (lub || rep || shp || shq) {
+    const double id = 1.0 / d;
+    const double n[3] = {rr[0] * id, rr[1] * id, rr[2] * id};
+    const double dU[3] = {Uj[0] - syij * rate * L[1] - Ui[0], Uj[1] - Ui[1],
+                          Uj[2] - Ui[2]};
 
-      const double4_32a VQ = A.vel[cur][q];
-      const double4_32a WQ = A.omg[cur][q];
-      const int tq = A.tag[cur][q];
-      const bool p_is_i = tp < tq;
-      // orient: i = lower tag, n and r from i to j
-      double rr[3], syij, ai, aj;
-      double Ui[3], Uj[3], Wi[3], Wj[3];
-      if (p_is_i) {
-        rr[0] = rpq[0]; rr[1] = rpq[1]; rr[2] = rpq[2]; syij = sy;
-        ai = ap; aj = Q.w;
-        Ui[0] = VP.x; Ui[1] = VP.y; Ui[2] = VP.z; Uj[0] = VQ.x; Uj[1] = VQ.y; Uj[2] = VQ.z;
-        Wi[0] = WP.x; Wi[1] = WP.y; Wi[2] = WP.z; Wj[0] = WQ.x; Wj[1] = WQ.y; Wj[2] = WQ.z;
-      } else {
-        rr[0] = -rpq[0]; rr[1] = -rpq[1]; rr[2] = -rpq[2]; syij = -sy;
-        ai = Q.w; aj = ap;
-        Ui[0] = VQ.x; Ui[1] = VQ.y; Ui[2] = VQ.z; Uj[0] = VP.x; Uj[1] = VP.y; Uj[2] = VP.z;
-        Wi[0] = WQ.x; Wi[1] = WQ.y; Wi[2] = WQ.z; Wj[0] = WP.x; Wj[1] = WP.y; Wj[2] = WP.z;
-      }
-      const double id = 1.0 / d;
-      const double n[3] = {rr[0] * id, rr[1] * id, rr[2] * id};
-      const double dU[3] = {Uj[0] - syij * rate * L[1] - Ui[0], Uj[1] - Ui[1],
-                            Uj[2] - Ui[2]};
+    if (SAMPLE && (shp || shq)) {
+      const double w = (shp ? 1.0 : 0.0) + (shq ? 1.0 : 0.0);
+#pragma unroll
+      for (int al = 0; al < 3; ++al)
+#pragma unroll
+        for (int be = 0; be < 3; ++be) sVir[(kStrOff + 3 * al + be) * kBlock + tid] += w * n[al] * n[be];
+    }
+    double FR[3] = {0.0, 0.0, 0.0};
+    if (rep) {
+      const double f = RP.rep_A / kappa * exp(-h / kappa);
+#pragma unroll
+      for (int q3 = 0; q3 < 3; ++q3) FR[q3] = -f * n[q3];
+    }
 
-      if (SAMPLE && (shp || shq)) {
-        const double w = (shp ? 1.0 : 0.0) + (shq ? 1.0 : 0.0);
+    PairOut<double> o;
+    if (lub && s.lubrication) {
+      const double xi_e = xi < s.xi_min ? s.xi_min : xi;
+      const double ixi = 1.0 / xi_e;
+      const double lg = log(ixi);
+      const Res8<double> R = resistances_rcp(eta, ai, aj, ixi, lg);
+      double g[6] = {0, 0, 0, 0, 0, 0};
+      const int li = (int)((p_is_i ? tp : tq) - t0);
+      const int lj = (int)((p_is_i ? tq : tp) - t0);
+      if (NOISE) gauss6_f64(key0, key1, k, (uint32_t)li, (uint32_t)lj, g);
+      lub_brownian<double, NOISE>(R, n, dU, Wi, Wj, g, g + 3, c, s.torque_sign, o);
+    } else {
 #pragma unroll
-        for (int al = 0; al < 3; ++al)
-#pragma unroll
-          for (int be = 0; be < 3; ++be) sVir[(kStrOff + 3 * al + be) * kBlock + tid] += w * n[al] * n[be];
-      }
-      double FR[3] = {0.0, 0.0, 0.0};
-      if (rep) {
-        const double f = RP.rep_A / kappa * exp(-h / kappa);
-#pragma unroll
-        for (int q3 = 0; q3 < 3; ++q3) FR[q3] = -f * n[q3];
-      }
+      for (int q3 = 0; q3 < 3; ++q3) o.FL[q3] = o.FB[q3] = o.Ti[q3] = o.Tj[q3] = 0.0;
+    }
 
-      PairOut<double> o;
-      if (lub && s.lubrication) {
-        const double xi_e = xi < s.xi_min ? s.xi_min : xi;
-        const double ixi = 1.0 / xi_e;
-        const double lg = log(ixi);
-        const Res8<double> R = resistances_rcp(eta, ai, aj, ixi, lg);
-        double g[6] = {0, 0, 0, 0, 0, 0};
-        const int li = (int)((p_is_i ? tp : tq) - t0);
-        const int lj = (int)((p_is_i ? tq : tp) - t0);
-        if (NOISE) gauss6_f64(key0, key1, k, (uint32_t)li, (uint32_t)lj, g);
-        lub_brownian<double, NOISE>(R, n, dU, Wi, Wj, g, g + 3, c, s.torque_sign, o);
-      } else {
-#pragma unroll
-        for (int q3 = 0; q3 < 3; ++q3) o.FL[q3] = o.FB[q3] = o.Ti[q3] = o.Tj[q3] = 0.0;
-      }
-
-      double FC[3] = {0.0, 0.0, 0.0}, TCi[3] = {0.0, 0.0, 0.0}, TCj[3] = {0.0, 0.0, 0.0};
-      if (h < 0.0 && s.contact) {
-        const double delta = -h;
-        double Ft[3] = {0.0, 0.0, 0.0};
-        if (FRIC && mu > 0.0) {
-          double xt[3] = {0.0, 0.0, 0.0};
-          const int64_t hi = (int64_t)sl * Np + po;
-          if ((A.cmsk[cur][po] >> sl) & 1ull) {
-            xt[0] = hist[hi]; xt[1] = hist[hi + hstride]; xt[2] = hist[hi + 2 * hstride];
-          }
-          if (s.advance) {
-            const double ww[3] = {ai * Wi[0] + aj * Wj[0], ai * Wi[1] + aj * Wj[1],
-                                  ai * Wi[2] + aj * Wj[2]};
-            double wxn[3];
-            cross3(ww, n, wxn);
-            const double v[3] = {dU[0] - wxn[0], dU[1] - wxn[1], dU[2] - wxn[2]};
-            history_update(xt, n, v, s.dt, kt, mu * kn * delta);
-          }
-          hist[hi] = xt[0]; hist[hi + hstride] = xt[1]; hist[hi + 2 * hstride] = xt[2];
-          atomicOr(&sM[tid - lane + ow], 1ull << sl);
-          Ft[0] = kt * xt[0]; Ft[1] = kt * xt[1]; Ft[2] = kt * xt[2];
+    double FC[3] = {0.0, 0.0, 0.0}, TCi[3] = {0.0, 0.0, 0.0}, TCj[3] = {0.0, 0.0, 0.0};
+    if (h < 0.0 && s.contact) {
+      const double delta = -h;
+      double Ft[3] = {0.0, 0.0, 0.0};
+      if (FRIC && mu > 0.0) {
+        double xt[3] = {0.0, 0.0, 0.0};
+        const int64_t hi = (int64_t)sl * Np + po;
+        if ((A.cmsk[cur][po] >> sl) & 1ull) {
+          xt[0] = hist[hi]; xt[1] = hist[hi + hstride]; xt[2] = hist[hi + 2 * hstride];
         }
-#pragma unroll
-        for (int q3 = 0; q3 < 3; ++q3) FC[q3] = -kn * delta * n[q3] + Ft[q3];
-        double nxF[3];
-        cross3(n, Ft, nxF);
-#pragma unroll
-        for (int q3 = 0; q3 < 3; ++q3) {
-          TCi[q3] = ai * nxF[q3];
-          TCj[q3] = aj * nxF[q3];
+        if (s.advance) {
+          const double ww[3] = {ai * Wi[0] + aj * Wj[0], ai * Wi[1] + aj * Wj[1],
+                                ai * Wi[2] + aj * Wj[2]};
+          double wxn[3];
+          cross3(ww, n, wxn);
+          const double v[3] = {dU[0] - wxn[0], dU[1] - wxn[1], dU[2] - wxn[2]};
+          history_update(xt, n, v, s.dt, kt, mu * kn * delta);
         }
+        hist[hi] = xt[0]; hist[hi + hstride] = xt[1]; hist[hi + 2 * hstride] = xt[2];
+        atomicOr(&sM[tid - lane + ow], 1ull << sl);
+        Ft[0] = kt * xt[0]; Ft[1] = kt * xt[1]; Ft[2] = kt * xt[2];
       }
-
-      double Fi[3], Ti_[3], Tj_[3];
+#pragma unroll
+      for (int q3 = 0; q3 < 3; ++q3) FC[q3] = -kn * delta * n[q3] + Ft[q3];
+      double nxF[3];
+      cross3(n, Ft, nxF);
 #pragma unroll
       for (int q3 = 0; q3 < 3; ++q3) {
-        Fi[q3] = FC[q3] + o.FL[q3] + o.FB[q3] + FR[q3];
-        Ti_[q3] = TCi[q3] + o.Ti[q3];
-        Tj_[q3] = TCj[q3] + o.Tj[q3];
-      }
-      const int64_t qo = q;
-      const double sgn = p_is_i ? 1.0 : -1.0;
-      const double* To = p_is_i ? Ti_ : Tj_;
-      const double* Tq = p_is_i ? Tj_ : Ti_;
-      if (DET) {
-        const int64_t e = (int64_t)sl * Np + po, KN = (int64_t)A.kmax * Np;
-#pragma unroll
-        for (int q3 = 0; q3 < 3; ++q3) {
-          A.det_slot[q3 * KN + e] = sgn * Fi[q3];
-          A.det_slot[(3 + q3) * KN + e] = To[q3];
-          A.det_slot[(6 + q3) * KN + e] = Tq[q3];
-        }
-      } else {
-#pragma unroll
-        for (int q3 = 0; q3 < 3; ++q3) {
-          atomicAdd(A.frc[cur] + q3 * Np + po, sgn * Fi[q3]);
-          atomicAdd(A.trq[cur] + q3 * Np + po, To[q3]);
-          atomicAdd(A.frc[cur] + q3 * Np + qo, -sgn * Fi[q3]);
-          atomicAdd(A.trq[cur] + q3 * Np + qo, Tq[q3]);
-        }
-      }
-      if (SAMPLE) {
-#pragma unroll
-        for (int al = 0; al < 3; ++al)
-#pragma unroll
-          for (int be = 0; be < 3; ++be) {
-            sVir[(3 * al + be) * kBlock + tid] += FC[al] * rr[be];
-            sVir[(9 + 3 * al + be) * kBlock + tid] += o.FL[al] * rr[be];
-            sVir[(18 + 3 * al + be) * kBlock + tid] += o.FB[al] * rr[be];
-            sVir[(kRepOff + 3 * al + be) * kBlock + tid] += FR[al] * rr[be];
-          }
-      }
-      } else if (DET) {
-        // a listed pair that does not interact: its slot holds zeros
-        const int64_t e = (int64_t)sl * Np + po, KN = (int64_t)A.kmax * Np;
-#pragma unroll
-        for (int c9 = 0; c9 < 9; ++c9) A.det_slot[c9 * KN + e] = 0.0;
+        TCi[q3] = ai * nxF[q3];
+        TCj[q3] = aj * nxF[q3];
       }
     }
+
+    double Fi[3], Ti_[3], Tj_[3];
+#pragma unroll
+    for (int q3 = 0; q3 < 3; ++q3) {
+      Fi[q3] = FC[q3] + o.FL[q3] + o.FB[q3] + FR[q3];
+      Ti_[q3] = TCi[q3] + o.Ti[q3];
+      Tj_[q3] = TCj[q3] + o.Tj[q3];
+    }
+    const int64_t qo = q;
+    const double sgn = p_is_i ? 1.0 : -1.0;
+    const double* To = p_is_i ? Ti_ : Tj_;
+    const double* Tq = p_is_i ? Tj_ : Ti_;
+    if (DET) {
+      const int64_t e = (int64_t)sl * Np + po, KN = (int64_t)A.kmax * Np;
+#pragma unroll
+      for (int q3 = 0; q3 < 3; ++q3) {
+        A.det_slot[q3 * KN + e] = sgn * Fi[q3];
+        A.det_slot[(3 + q3) * KN + e] = To[q3];
+        A.det_slot[(6 + q3) * KN + e] = Tq[q3];
+      }
+    } else {
+#pragma unroll
+      for (int q3 = 0; q3 < 3; ++q3) {
+        atomicAdd(A.frc[cur] + q3 * Np + po, sgn * Fi[q3]);
+        atomicAdd(A.trq[cur] + q3 * Np + po, To[q3]);
+        atomicAdd(A.frc[cur] + q3 * Np + qo, -sgn * Fi[q3]);
+        atomicAdd(A.trq[cur] + q3 * Np + qo, Tq[q3]);
+      }
+    }
+    if (SAMPLE) {
+#pragma unroll
+      for (int al = 0; al < 3; ++al)
+#pragma unroll
+        for (int be = 0; be < 3; ++be) {
+          sVir[(3 * al + be) * kBlock + tid] += FC[al] * rr[be];
+          sVir[(9 + 3 * al + be) * kBlock + tid] += o.FL[al] * rr[be];
+          sVir[(18 + 3 * al + be) * kBlock + tid] += o.FB[al] * rr[be];
+          sVir[(kRepOff + 3 * al + be) * kBlock + tid] += FR[al] * rr[be];
+        }
+    }
+    } else if (DET) {
+      // a listed pair that does not interact: its slot holds zeros
+      const int64_t e = (int64_t)sl * Np + po, KN = (int64_t)A.kmax * Np;
+#pragma unroll
+      for (int c9 = 0; c9 < 9; ++c9) A.det_slot[c9 * KN + e] = 0.0;
+    }
+  };
+
+  // Work loop of the warp, all decisions warp-uniform.  A pass reads the next
+  // 32 list items and queues those within the widest interaction range
+  // (touching pairs apart from the others) in two 64-entry rings in shared
+  // memory; a batch runs 32 queued pairs of one ring, one per lane, so pairs
+  // beyond the range and the contact branch leave no lanes idle through the
+  // FP64 arithmetic.  What is left at the end runs as one or two batches.
+  constexpr int kQ = 64;
+  __shared__ int qE[2][kBlock / 32][kQ];   // ow | sl << 5
+  const int warp = tid >> 5;
+  // the range test widened by a relative 1e-9 above the rounding of the
+  // exact tests, which decide in item()
+  const double rcf = 1.0 + 0.5 * s.xi_max;
+  const bool rep_any = s.rep_on && RP.rep_A > 0.0;
+  const double repf = 1.0 + 0.01 * s.rep_cut;
+  const bool strc = SAMPLE && s.structural;
+  int h0 = 0, n0 = 0, h1 = 0, n1 = 0, base = 0;
+  while (true) {
+    int c0 = 0, c1 = 0;
+    if (n0 >= 32) {
+      c0 = 32;
+    } else if (n1 >= 32) {
+      c1 = 32;
+    } else if (base < total) {
+      const int t = base + lane;
+      // owner row o of item t: the number of rows ending at or before t
+      int ow = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int v = __shfl_sync(0xffffffffu, incl, ow + step - 1);
+        if (v <= t) ow += step;
+      }
+      const int sl = t - __shfl_sync(0xffffffffu, excl, ow);
+      bool keep = false, touch = false;
+      if (t < total) {
+        const int po = pw + ow;
+        const int q = A.nbr[cur][(int64_t)sl * Np + po] & kNbrIndexMask;
+        const double4_32a P = A.pos[cur][po];
+        const double4_32a Q = A.pos[cur][q];
+        double rpq[3], sy;
+        min_image_f64(Q.x - P.x, Q.y - P.y, Q.z - P.z, L, iL, tilt, rpq, &sy);
+        const double d2 = rpq[0] * rpq[0] + rpq[1] * rpq[1] + rpq[2] * rpq[2];
+        const double S = P.w + Q.w;
+        double rc = S * rcf;
+        if (rep_any) rc = fmax(rc, S * repf);
+        if (strc) rc = fmax(rc, S + s.shell * fmax(P.w, Q.w));
+        keep = d2 <= rc * rc * (1.0 + 1e-9);
+        touch = keep && d2 <= S * S * (1.0 + 1e-9);
+        if (DET && !keep) {
+          // a listed pair beyond every range: its slot holds zeros
+          const int64_t e = (int64_t)sl * Np + po, KN = (int64_t)A.kmax * Np;
+#pragma unroll
+          for (int c9 = 0; c9 < 9; ++c9) A.det_slot[c9 * KN + e] = 0.0;
+        }
+      }
+      const unsigned m0 = __ballot_sync(0xffffffffu, keep && !touch);
+      const unsigned m1 = __ballot_sync(0xffffffffu, touch);
+      if (keep) {
+        const unsigned below = (1u << lane) - 1u;
+        const int e = touch ? (h1 + n1 + __popc(m1 & below)) & (kQ - 1)
+                            : (h0 + n0 + __popc(m0 & below)) & (kQ - 1);
+        qE[touch ? 1 : 0][warp][e] = ow | (sl << 5);
+      }
+      n0 += __popc(m0);
+      n1 += __popc(m1);
+      __syncwarp();
+      base += 32;
+      continue;
+    } else if (n0 + n1 > 32) {
+      c1 = n1;   // the touching pairs first, then the rest in one batch
+    } else if (n0 + n1 > 0) {
+      c0 = n0;
+      c1 = n1;
+    } else {
+      break;
+    }
+    // lanes [0, c0) take ring 0 from its head, lanes [c0, c0 + c1) ring 1
+    if (lane < c0 + c1) {
+      const int qi = lane < c0 ? 0 : 1;
+      const int e = qi ? (h1 + lane - c0) & (kQ - 1) : (h0 + lane) & (kQ - 1);
+      const int v = qE[qi][warp][e];
+      item(v & 31, v >> 5);
+    }
+    __syncwarp();
+    h0 = (h0 + c0) & (kQ - 1);
+    n0 -= c0;
+    h1 = (h1 + c1) & (kQ - 1);
+    n1 -= c1;
   }
   __syncwarp();
   if (FRIC && active) A.cmsk[cur][p] = sM[tid];
