@@ -618,6 +618,33 @@ void launch_reduce(susp_t* h, int sample_pair, int sample_kin, int ppar, cudaStr
         [&] { launch_reduce_stress(h->A, h->bm, sample_pair, sample_kin, ppar, st); });
 }
 
+// The rebuild's kernels captured as one graph and launched on st, the way a
+// step graph runs them as a conditional node (one launch for the host, no
+// gaps between the kernels); eager launches where capture is not possible
+// (st already capturing).  The graph is destroyed at once: its launch
+// completes on its own.
+void launch_rebuild_graph(susp_t* h, const StepArgs& s, cudaStream_t st) {
+  const int mixed = h->p0.precision == SUSP_MIXED;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone &&
+      cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    launch_rebuild(h->A, h->bm, s, st, mixed);
+    if (cudaStreamEndCapture(st, &g) == cudaSuccess && g &&
+        cudaGraphInstantiate(&ge, g, 0) != cudaSuccess)
+      ge = nullptr;
+  }
+  if (ge) {
+    cudaGraphLaunch(ge, st);
+    cudaGraphExecDestroy(ge);
+  } else {
+    cudaGetLastError();
+    launch_rebuild(h->A, h->bm, s, st, mixed);
+  }
+  if (g) cudaGraphDestroy(g);
+}
+
 // kernels in one neighbour rebuild (gated sequence of k_neighbors.cu)
 int rebuild_kernels(const susp_t* h, const StepArgs& s) {
   return 11 + (s.friction ? 1 : 0) + (h->p0.precision == SUSP_MIXED ? 1 : 0) +
@@ -693,9 +720,9 @@ void enqueue_steps(susp_t* h, int64_t first, int64_t n, double dt,
       cudaMemcpyAsync(&need, &h->A.ctl->need_rebuild, sizeof(int), cudaMemcpyDeviceToHost, st);
       cudaStreamSynchronize(st);
       if (need) {
-        timed(h, kFamRebuild, st, [&] {
-          launch_rebuild(h->A, h->bm, s, st, h->p0.precision == SUSP_MIXED);
-        });
+        // one graph launch, so that the events time the device work and not
+        // the host's launch of each kernel
+        timed(h, kFamRebuild, st, [&] { launch_rebuild_graph(h, s, st); });
         h->launches += rebuild_kernels(h, s);
       }
     } else {
@@ -1395,7 +1422,7 @@ int susp_build_neighbors(susp_t* h) {
   CK(cudaSetDevice(h->dev));
   StepArgs s = make_args(h, h->last_dt, 0, 0);
   launch_request_rebuild(h->A, h->stream);
-  launch_rebuild(h->A, h->bm, s, h->stream, h->p0.precision == SUSP_MIXED);
+  launch_rebuild_graph(h, s, h->stream);
   return check_errors(h);
 }
 
