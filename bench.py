@@ -539,14 +539,19 @@ def run_scaling(susp, stream, inner=100, steps=3):
             for _ in range(steps):
                 s.step(inner, p["shear_rate"], p["kT"], p["dt"], p["seed"])
         ms = _timed(stream, run)
-        prof = s.profile(inner, p["dt"])
+        # long enough to hold a rebuild (about every 250 steps)
+        prof = s.profile(max(inner, 400), p["dt"])
         info = s.info()
         ij, _ = s.history()
         K, c = info["npairs"] / N, len(ij) / N
         pb = algorithmic_bytes("pair", "mixed", K, c, True)
         pair_ms = prof["pair"]["ms_per_launch"]
-        # one explicit rebuild (the kernels a due rebuild runs), timed alone
-        rb_ms = _timed(stream, s.build_neighbors)
+        # a due rebuild's device time in the profiled steps (one graph
+        # launch), else one explicit rebuild timed around the call
+        if prof["rebuild"]["launches"] > 0:
+            rb_ms = prof["rebuild"]["ms_per_launch"]
+        else:
+            rb_ms = _timed(stream, s.build_neighbors)
         rbb = rebuild_bytes(K)
         out[f"{N // 1000000}M"] = {
             "N": N, "tiles": list(ks), "value": round(N * inner * steps / (ms / 1e3), 1),

@@ -618,31 +618,37 @@ void launch_reduce(susp_t* h, int sample_pair, int sample_kin, int ppar, cudaStr
         [&] { launch_reduce_stress(h->A, h->bm, sample_pair, sample_kin, ppar, st); });
 }
 
-// The rebuild's kernels captured as one graph and launched on st, the way a
-// step graph runs them as a conditional node (one launch for the host, no
-// gaps between the kernels); eager launches where capture is not possible
-// (st already capturing).  The graph is destroyed at once: its launch
-// completes on its own.
-void launch_rebuild_graph(susp_t* h, const StepArgs& s, cudaStream_t st) {
-  const int mixed = h->p0.precision == SUSP_MIXED;
+// The rebuild's kernels captured as one graph, instantiated and uploaded to
+// the device, ready to launch on st the way a step graph runs them as a
+// conditional node (one launch for the host, no gaps between the kernels);
+// nullptr where capture is not possible (st already capturing).
+cudaGraphExec_t prepare_rebuild_graph(susp_t* h, const StepArgs& s, cudaStream_t st) {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ge = nullptr;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone &&
       cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-    launch_rebuild(h->A, h->bm, s, st, mixed);
+    launch_rebuild(h->A, h->bm, s, st, h->p0.precision == SUSP_MIXED);
     if (cudaStreamEndCapture(st, &g) == cudaSuccess && g &&
-        cudaGraphInstantiate(&ge, g, 0) != cudaSuccess)
+        (cudaGraphInstantiate(&ge, g, 0) != cudaSuccess || cudaGraphUpload(ge, st) != cudaSuccess)) {
+      if (ge) cudaGraphExecDestroy(ge);
       ge = nullptr;
+    }
   }
+  if (g) cudaGraphDestroy(g);
+  if (!ge) cudaGetLastError();
+  return ge;
+}
+
+// Launches a prepared rebuild graph (and destroys it: the launch completes on
+// its own), or the rebuild's kernels one by one where there is none.
+void launch_rebuild_prepared(susp_t* h, const StepArgs& s, cudaStream_t st, cudaGraphExec_t ge) {
   if (ge) {
     cudaGraphLaunch(ge, st);
     cudaGraphExecDestroy(ge);
   } else {
-    cudaGetLastError();
-    launch_rebuild(h->A, h->bm, s, st, mixed);
+    launch_rebuild(h->A, h->bm, s, st, h->p0.precision == SUSP_MIXED);
   }
-  if (g) cudaGraphDestroy(g);
 }
 
 // kernels in one neighbour rebuild (gated sequence of k_neighbors.cu)
@@ -722,7 +728,8 @@ void enqueue_steps(susp_t* h, int64_t first, int64_t n, double dt,
       if (need) {
         // one graph launch, so that the events time the device work and not
         // the host's launch of each kernel
-        timed(h, kFamRebuild, st, [&] { launch_rebuild_graph(h, s, st); });
+        cudaGraphExec_t ge = prepare_rebuild_graph(h, s, st);
+        timed(h, kFamRebuild, st, [&] { launch_rebuild_prepared(h, s, st, ge); });
         h->launches += rebuild_kernels(h, s);
       }
     } else {
@@ -1422,7 +1429,7 @@ int susp_build_neighbors(susp_t* h) {
   CK(cudaSetDevice(h->dev));
   StepArgs s = make_args(h, h->last_dt, 0, 0);
   launch_request_rebuild(h->A, h->stream);
-  launch_rebuild_graph(h, s, h->stream);
+  launch_rebuild_prepared(h, s, h->stream, prepare_rebuild_graph(h, s, h->stream));
   return check_errors(h);
 }
 

@@ -51,13 +51,12 @@ __device__ __forceinline__ void store_df3(double4_32a* base, int64_t p, const DF
 // Mirrors of one sphere (see the file comment): pm[0]/pm[1] are the hi/lo
 // halves of (offset, radius).  `ct` is tilt/ncy and `tilt` the tilt, both
 // double-float, of the box the positions are wrapped in.
-__device__ __forceinline__ void make_mirrors(const Replica& R, df tilt, df ct, int cellkey,
+__device__ __forceinline__ void make_mirrors(const Replica& R, df tilt, df ct, int pack,
                                              const DF3& x, df a, const DF3& U,
                                              const DF3& W, int tag, float4* pm,
                                              float4& vm, float4& om) {
-  const int local = cellkey - (int)R.cell_base;
-  const int cx = local % R.nc[0], cy = (local / R.nc[0]) % R.nc[1],
-            cz = local / (R.nc[0] * R.nc[1]);
+  // home cell coordinates, packed 10 bits per axis by the rebuild
+  const int cx = pack & 1023, cy = (pack >> 10) & 1023, cz = pack >> 20;
   // home-cell origin in the lab frame
   const df ox = df_add(df_mul_f(df{R.cw_hi[0], R.cw_lo[0]}, (float)cx), df_mul_f(ct, (float)cy));
   const df oy = df_mul_f(df{R.cw_hi[1], R.cw_lo[1]}, (float)cy);
@@ -80,8 +79,6 @@ __device__ __forceinline__ void make_mirrors(const Replica& R, df tilt, df ct, i
   const df yrel = df_sub(x.y, df{R.yc_hi, R.yc_lo});
   const df ux = df_sub(U.x, df_mul(yrel, df{R.rate_hi, R.rate_lo}));
   vm = make_float4(df_to_f(ux), df_to_f(U.y), df_to_f(U.z), __int_as_float(tag));
-  // home cell coordinates packed 10 bits each (nc <= 1023 per axis)
-  const int pack = cx | (cy << 10) | (cz << 20);
   om = make_float4(df_to_f(W.x), df_to_f(W.y), df_to_f(W.z), __int_as_float(pack));
 }
 
@@ -168,14 +165,14 @@ k_integrate_mixed(Arrays A, BlockMap bm, StepArgs s, int close, int sample_kin,
   DF3 x{}, U{}, W{};
   float a = 0.0f, alo = 0.0f, im = 0.0f, iI = 0.0f;
   float4 f = make_float4(0.f, 0.f, 0.f, 0.f), t = f;
-  int cellkey = 0, tagp = 0;
+  int cellpk = 0, tagp = 0;
   float4* F4 = reinterpret_cast<float4*>(A.frc[cur]);
   float4* T4 = reinterpret_cast<float4*>(A.trq[cur]);
   if (active) {
     load_df3(A.pos[cur], p, x, a, &alo);
     load_df3(A.vel[cur], p, U, im);
     load_df3(A.omg[cur], p, W, iI);
-    cellkey = A.cell[p];
+    cellpk = A.cell[p];
     tagp = A.tag[cur][p];
   }
   // the state above is not written by the pair kernel; the forces are, and
@@ -229,7 +226,7 @@ k_integrate_mixed(Arrays A, BlockMap bm, StepArgs s, int close, int sample_kin,
     F4[p] = make_float4(0.f, 0.f, 0.f, 0.f);
     T4[p] = make_float4(0.f, 0.f, 0.f, 0.f);
     float4 pm[2], vm, om;
-    make_mirrors(RP, tilt, ct, cellkey, x, df{a, alo}, U, W, tagp, pm, vm, om);
+    make_mirrors(RP, tilt, ct, cellpk, x, df{a, alo}, U, W, tagp, pm, vm, om);
     A.posm[2 * p] = pm[0];
     A.posm[2 * p + 1] = pm[1];
     A.velm[p] = vm;

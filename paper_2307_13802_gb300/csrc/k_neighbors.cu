@@ -41,12 +41,16 @@ __global__ void k_zero_counts(Arrays A) {
     A.cell_count[i] = 0;
 }
 
+// Fractional coordinates by the reciprocal edges (an ulp from the quotients;
+// the cells are sized with a relative guard of 1e-9 above the list cutoff,
+// so the stencil still covers every pair), which keeps FP64 divisions off
+// the rebuild.
 __device__ __forceinline__ int cell_index(const Replica& R, double x, double y,
                                           double z, int* c3) {
-  const double sy = y / R.L[1];
-  double sx = (x - R.tilt * sy) / R.L[0];
+  const double sy = y * R.iL[1];
+  double sx = (x - R.tilt * sy) * R.iL[0];
   sx = sx - floor(sx);
-  const double sz = z / R.L[2];
+  const double sz = z * R.iL[2];
   int cx = (int)(sx * R.nc[0]);
   int cy = (int)(sy * R.nc[1]);
   int cz = (int)(sz * R.nc[2]);
@@ -212,9 +216,21 @@ __global__ void k_permute(Arrays A) {
   }
   const int t = A.tag[cur][o];
   A.tag[nxt][p] = t;
-  A.rep[nxt][p] = A.rep[cur][o];
-  A.cell[p] = A.key[o];
+  const int r = A.rep[cur][o];
+  A.rep[nxt][p] = r;
+  // home cell coordinates packed 10 bits per axis (at most 1023 cells per
+  // edge), decoded once here instead of at every step
+  const Replica& R = A.repl[r];
+  const int local = (int)(A.key[o] - R.cell_base);
+  const int cx = local % R.nc[0], cy = (local / R.nc[0]) % R.nc[1],
+            cz = local / (R.nc[0] * R.nc[1]);
+  A.cell[p] = cx | (cy << 10) | (cz << 20);
   A.slot_of_tag[t] = (int)p;
+}
+
+// neighbour cell index along one axis, periodic (|d| <= 1, n >= 3)
+__device__ __forceinline__ int wrap_cell(int i, int n) {
+  return i < 0 ? i + n : (i >= n ? i - n : i);
 }
 
 __global__ void __launch_bounds__(kBlock) k_build_list(Arrays A, StepArgs s, double rc_fac) {
@@ -224,9 +240,9 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Arrays A, StepArgs s, dou
   if (p >= A.N) return;
   const int r = A.rep[nxt][p];
   const Replica& R = A.repl[r];
-  const int local = (int)(A.cell[p] - R.cell_base);
   const int ncx = R.nc[0], ncy = R.nc[1], ncz = R.nc[2];
-  const int cx = local % ncx, cy = (local / ncx) % ncy, cz = local / (ncx * ncy);
+  const int pk = A.cell[p];
+  const int cx = pk & 1023, cy = (pk >> 10) & 1023, cz = pk >> 20;
   const int64_t Np = A.Npad;
   int* row = A.nbr[nxt] + p;
   int cnt = 0;
@@ -245,30 +261,60 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Arrays A, StepArgs s, dou
     const float margin = 1e-6f * fmaxf(Lf[0], fmaxf(Lf[1], Lf[2]));
     const float fac = (float)rc_fac, rfac = s.rep_on ? (float)s.rep_fac : 0.0f;
     const float shell = s.structural ? (float)s.shell : 0.0f, skin = (float)s.skin;
+    const float4* __restrict__ PQ = reinterpret_cast<const float4*>(A.pos[nxt]);
+    const int* __restrict__ cs = A.cell_start;
     for (int dz = -1; dz <= 1; ++dz) {
-      const int zz = (cz + dz + ncz) % ncz;
+      const int zz = wrap_cell(cz + dz, ncz);
       for (int dy = -1; dy <= 1; ++dy) {
-        const int yy = (cy + dy + ncy) % ncy;
-        for (int dx = -1; dx <= 1; ++dx) {
-          const int xx = (cx + dx + ncx) % ncx;
-          const int64_t key = R.cell_base + ((int64_t)zz * ncy + yy) * ncx + xx;
-          const int q0 = A.cell_start[key], q1 = A.cell_start[key + 1];
-          for (int q = q0; q < q1; ++q) {
-            if (q <= p) continue;
-            const float4 Q = reinterpret_cast<const float4*>(A.pos[nxt])[2 * q];
-            float ry = Q.y - P.y, rx = Q.x - P.x, rz = Q.z - P.z;
-            const float sy = rintf(ry * iLf[1]);
-            ry -= sy * Lf[1];
-            rx -= sy * tiltf;
-            rx -= rintf(rx * iLf[0]) * Lf[0];
-            rz -= rintf(rz * iLf[2]) * Lf[2];
-            const float S = P.w + Q.w;
-            const float rc = fmaxf(fmaxf(S * fac, S * rfac), S + shell * fmaxf(P.w, Q.w)) +
-                             skin + margin + 1e-5f * S;
-            if (!(rx * rx + ry * ry + rz * rz < rc * rc)) continue;
-            const int code = (dx + 1) * 3 + (dy + 1) + 9 * (dz + 1);
-            if (cnt < kmax) row[(int64_t)cnt * Np] = q | (code << kNbrIndexBits);
-            ++cnt;
+        const int yy = wrap_cell(cy + dy, ncy);
+        const int64_t rowkey = R.cell_base + ((int64_t)zz * ncy + yy) * ncx;
+        // The three cells of the stencil row are one range of the sorted
+        // order unless the row wraps in x; dx of a partner is then
+        // -1 + (q >= b1) + (q >= b2).  Candidates are tested four at a time,
+        // their records loaded together so that the loads overlap.
+        const bool merged = cx >= 1 && cx + 1 < ncx;
+        for (int part = 0; part < (merged ? 1 : 3); ++part) {
+          int lo, hi, dx0, b1, b2;
+          if (merged) {
+            const int64_t k0 = rowkey + cx - 1;
+            lo = cs[k0];
+            b1 = cs[k0 + 1];
+            b2 = cs[k0 + 2];
+            hi = cs[k0 + 3];
+            dx0 = -1;
+          } else {
+            dx0 = part - 1;
+            const int64_t k = rowkey + wrap_cell(cx + dx0, ncx);
+            lo = cs[k];
+            hi = cs[k + 1];
+            b1 = b2 = 0x7fffffff;
+          }
+          // the half list: partners after p in the sorted order
+          for (int q = max(lo, (int)p + 1); q < hi; q += 4) {
+            float4 Qv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              Qv[u] = q + u < hi ? PQ[2 * (q + u)] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int qq = q + u;
+              if (qq >= hi) break;
+              const float4 Q = Qv[u];
+              float ry = Q.y - P.y, rx = Q.x - P.x, rz = Q.z - P.z;
+              const float sy = rintf(ry * iLf[1]);
+              ry -= sy * Lf[1];
+              rx -= sy * tiltf;
+              rx -= rintf(rx * iLf[0]) * Lf[0];
+              rz -= rintf(rz * iLf[2]) * Lf[2];
+              const float S = P.w + Q.w;
+              const float rc = fmaxf(fmaxf(S * fac, S * rfac), S + shell * fmaxf(P.w, Q.w)) +
+                               skin + margin + 1e-5f * S;
+              if (!(rx * rx + ry * ry + rz * rz < rc * rc)) continue;
+              const int dx = dx0 + (qq >= b1 ? 1 : 0) + (qq >= b2 ? 1 : 0);
+              const int code = (dx + 1) * 3 + (dy + 1) + 9 * (dz + 1);
+              if (cnt < kmax) row[(int64_t)cnt * Np] = qq | (code << kNbrIndexBits);
+              ++cnt;
+            }
           }
         }
       }
@@ -279,15 +325,15 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Arrays A, StepArgs s, dou
     const double tilt = R.tilt;
     const double4_32a P = A.pos[nxt][p];
     for (int dz = -1; dz <= 1; ++dz) {
-      const int zz = (cz + dz + ncz) % ncz;
+      const int zz = wrap_cell(cz + dz, ncz);
       for (int dy = -1; dy <= 1; ++dy) {
-        const int yy = (cy + dy + ncy) % ncy;
+        const int yy = wrap_cell(cy + dy, ncy);
         for (int dx = -1; dx <= 1; ++dx) {
-          const int xx = (cx + dx + ncx) % ncx;
+          const int xx = wrap_cell(cx + dx, ncx);
           const int64_t key = R.cell_base + ((int64_t)zz * ncy + yy) * ncx + xx;
-          const int q0 = A.cell_start[key], q1 = A.cell_start[key + 1];
+          // the half list: partners after p in the sorted order
+          const int q0 = max(A.cell_start[key], (int)p + 1), q1 = A.cell_start[key + 1];
           for (int q = q0; q < q1; ++q) {
-            if (q <= p) continue;
             const double4_32a Q = A.pos[nxt][q];
             double rr[3], sy;
             min_image_f64(Q.x - P.x, Q.y - P.y, Q.z - P.z, L, iL, tilt, rr, &sy);
@@ -312,15 +358,22 @@ __global__ void __launch_bounds__(kBlock) k_build_list(Arrays A, StepArgs s, dou
       }
     }
   }
+  // the longest row and the number of pairs, summed over the warp first:
+  // one atomic per warp on each counter (one per sphere serialises a
+  // million updates of the same word)
+  const int full = cnt;
   if (cnt > kmax) {
     atomicOr(&A.ctl->err, kErrOverflow);
-    atomicMax(&A.ctl->max_row, cnt);
     cnt = kmax;
-  } else {
-    atomicMax(&A.ctl->max_row, cnt);
   }
   A.nnb[nxt][p] = cnt;
-  atomicAdd((unsigned long long*)&A.ctl->npairs, (unsigned long long)cnt);
+  const unsigned am = __activemask();
+  const int wmax = __reduce_max_sync(am, full);
+  const unsigned wsum = __reduce_add_sync(am, (unsigned)cnt);
+  if ((threadIdx.x & 31) == __ffs(am) - 1) {
+    atomicMax(&A.ctl->max_row, wmax);
+    atomicAdd((unsigned long long*)&A.ctl->npairs, (unsigned long long)wsum);
+  }
 }
 
 // carry tangential history of touching pairs into the new list

@@ -197,7 +197,8 @@ struct Arrays {
   int* rev_off;         // [N + 1] offsets into rev_ent
   int* rev_ent;         // [kmax * Npad] slots (sl * Npad + p) of each partner
   int* rev_part;        // scan block totals
-  int* cell;            // home cell of sorted particle (new order after build)
+  int* cell;            // home cell of sorted particle (new order after build),
+                        // coordinates packed cx | cy << 10 | cz << 20
   float4* posm;         // mixed-precision mirrors
   float4* velm;
   float4* omgm;
