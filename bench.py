@@ -200,9 +200,10 @@ def rebuild_bytes(K: float, passes: int = 2) -> float:
 def layout_bytes(family: str, precision: str, K: float, c: float, fric: bool) -> float:
     """Bytes the library's own layout moves per sphere in a launch (what the
     DRAM traffic is compared with): the mixed path's double-float position
-    records (32 B with the low words), velocity + tag and spin + packed cell
-    (16 B each), float4 force and torque accumulators (32 B), and the 64-bit
-    contact mask (16 B read and written) beside the 32-byte history records."""
+    records (32 B with the low words), the velocity + tag mirror and the high
+    half of the spin record (16 B each), float4 force and torque accumulators
+    (32 B), and the 64-bit contact mask (16 B read and written) beside the
+    32-byte history records.  The integrator writes two mirrors (48 B)."""
     hist = (16.0 + 48.0 * c) if fric else 0.0
     if family == "pair":
         if precision == "mixed":
@@ -210,7 +211,7 @@ def layout_bytes(family: str, precision: str, K: float, c: float, fric: bool) ->
         return 96.0 + 8.0 + 4.0 * K + 48.0 + hist
     if family == "integrate":
         if precision == "mixed":
-            return 96.0 + 32.0 + 8.0 + 96.0 + 64.0 + 32.0
+            return 96.0 + 32.0 + 8.0 + 96.0 + 48.0 + 32.0
         return 96.0 + 48.0 + 96.0 + 48.0
     return 0.0
 

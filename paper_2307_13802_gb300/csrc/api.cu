@@ -418,7 +418,6 @@ int allocate(susp_t* h) {
   if (h->p0.precision == SUSP_MIXED) {
     ok &= alloc_n(h, &A.posm, 2 * Np);  // 32-byte (hi, lo) records
     ok &= alloc_n(h, &A.velm, Np);
-    ok &= alloc_n(h, &A.omgm, Np);
   }
   int *brep = nullptr, *bst = nullptr, *ben = nullptr;
   ok &= alloc_n(h, &brep, nb);

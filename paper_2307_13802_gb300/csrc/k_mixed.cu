@@ -13,10 +13,10 @@
 //          nearest periodic image.  Offsets are a few cell widths at most, so
 //          the pair kernel rebuilds separations and the gap
 //          h = (d^2 - S^2)/(d + S) to ~1e-12 for any box size;
-//   velm = (U - U_inf(y), tag): velocity relative to the imposed flow;
-//   omgm = (Omega, home cell coordinates packed 10 bits per axis; the pair
-//          kernel takes cell offsets from the list entries instead, so the
-//          packed cell only labels the record).
+//   velm = (U - U_inf(y), tag): velocity relative to the imposed flow.
+// The pair kernel reads the spins from the high halves of the double-float
+// records themselves (a normalised double-float's high word is its value in
+// single precision), so they need no mirror.
 #include <cuda_runtime.h>
 
 #include "device_common.cuh"
@@ -52,9 +52,8 @@ __device__ __forceinline__ void store_df3(double4_32a* base, int64_t p, const DF
 // halves of (offset, radius).  `ct` is tilt/ncy and `tilt` the tilt, both
 // double-float, of the box the positions are wrapped in.
 __device__ __forceinline__ void make_mirrors(const Replica& R, df tilt, df ct, int pack,
-                                             const DF3& x, df a, const DF3& U,
-                                             const DF3& W, int tag, float4* pm,
-                                             float4& vm, float4& om) {
+                                             const DF3& x, df a, const DF3& U, int tag,
+                                             float4* pm, float4& vm) {
   // home cell coordinates, packed 10 bits per axis by the rebuild
   const int cx = pack & 1023, cy = (pack >> 10) & 1023, cz = pack >> 20;
   // home-cell origin in the lab frame
@@ -79,7 +78,6 @@ __device__ __forceinline__ void make_mirrors(const Replica& R, df tilt, df ct, i
   const df yrel = df_sub(x.y, df{R.yc_hi, R.yc_lo});
   const df ux = df_sub(U.x, df_mul(yrel, df{R.rate_hi, R.rate_lo}));
   vm = make_float4(df_to_f(ux), df_to_f(U.y), df_to_f(U.z), __int_as_float(tag));
-  om = make_float4(df_to_f(W.x), df_to_f(W.y), df_to_f(W.z), __int_as_float(pack));
 }
 
 __device__ __forceinline__ bool wrap_df(DF3& x, df& ux, const Replica& R, df tilt) {
@@ -225,12 +223,11 @@ k_integrate_mixed(Arrays A, BlockMap bm, StepArgs s, int close, int sample_kin,
     store_df3(A.omg[cur], p, W, iI);
     F4[p] = make_float4(0.f, 0.f, 0.f, 0.f);
     T4[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 pm[2], vm, om;
-    make_mirrors(RP, tilt, ct, cellpk, x, df{a, alo}, U, W, tagp, pm, vm, om);
+    float4 pm[2], vm;
+    make_mirrors(RP, tilt, ct, cellpk, x, df{a, alo}, U, tagp, pm, vm);
     A.posm[2 * p] = pm[0];
     A.posm[2 * p + 1] = pm[1];
     A.velm[p] = vm;
-    A.omgm[p] = om;
     vpec = sqrtf(vm.x * vm.x + vm.y * vm.y + vm.z * vm.z);
     if (!(vpec == vpec)) vpec = 0.0f;
   }
@@ -340,13 +337,12 @@ __global__ void k_mirror_mixed(Arrays A, int gated, int use_next) {
   load_df3(A.vel[c], p, U, im);
   load_df3(A.omg[c], p, W, iI);
   const df tilt = df_from_d(R.tilt);  // off the per-step path
-  float4 pm[2], vm, om;
-  make_mirrors(R, tilt, df{R.ct_hi, R.ct_lo}, A.cell[p], x, df{a, alo}, U, W, A.tag[c][p],
-               pm, vm, om);
+  float4 pm[2], vm;
+  make_mirrors(R, tilt, df{R.ct_hi, R.ct_lo}, A.cell[p], x, df{a, alo}, U, A.tag[c][p], pm,
+               vm);
   A.posm[2 * p] = pm[0];
   A.posm[2 * p + 1] = pm[1];
   A.velm[p] = vm;
-  A.omgm[p] = om;
 }
 
 // Host state (tag order, doubles) into the live copy in double-float form.

@@ -234,7 +234,9 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   float4* __restrict__ T4 = reinterpret_cast<float4*>(A.trq[cur]);
   const float4* __restrict__ PM = A.posm;
   const float4* __restrict__ VM = A.velm;
-  const float4* __restrict__ OM = A.omgm;
+  // spins: the high halves of the double-float records (a normalised
+  // double-float's high word is its value rounded to single precision)
+  const float4* __restrict__ OMD = reinterpret_cast<const float4*>(A.omg[cur]);
   const int* __restrict__ nbr = A.nbr[cur];
   // tangential history: one 32-byte record per list slot,
   // (x_hi, x_lo, y_hi, y_lo), (z_hi, z_lo, -, -)
@@ -249,7 +251,7 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
       nn = A.nnb[cur][p];
       if (FRIC) cm_own = A.cmsk[cur][p];
       if (s.onebody) {
-        const float4 P = PM[2 * p], V = VM[p], W = OM[p];
+        const float4 P = PM[2 * p], V = VM[p], W = OMD[2 * p];
         const float a = P.w;
         const float gt = 6.0f * pi * eta * a;
         const float gr = 8.0f * pi * eta * a * a * a;
@@ -310,7 +312,7 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
     const float xi = 2.0f * h / S;
     const int po = pb + warp * 32 + o;
     const float ap = sA[tid - lane + o];
-    const float4 WPo = __ldg(OM + po), WQ = __ldg(OM + q);
+    const float4 WPo = __ldg(OMD + 2 * po), WQ = __ldg(OMD + 2 * q);
     const float4 VPo = __ldg(VM + po), VQ = __ldg(VM + q);
     const int tp = __float_as_int(VPo.w), tq = __float_as_int(VQ.w);
     const bool p_is_i = tp < tq;

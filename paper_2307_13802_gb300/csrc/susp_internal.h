@@ -22,8 +22,9 @@
 //   cmsk uint64 [Npad]                    slot s in contact at last evaluation
 //   mirror (mixed precision)  posm: two float4 (hi, lo) of (dx, dy, dz, a),
 //                               the offset from the home-cell origin;
-//                               float4 velm (u - U_inf, tag); float4 omgm
-//                               (W, packed home cell); int32 cell (home key)
+//                               float4 velm (u - U_inf, tag); the spins
+//                               are read from the high halves of omg;
+//                               int32 cell (packed home cell coordinates)
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -199,9 +200,8 @@ struct Arrays {
   int* rev_part;        // scan block totals
   int* cell;            // home cell of sorted particle (new order after build),
                         // coordinates packed cx | cy << 10 | cz << 20
-  float4* posm;         // mixed-precision mirrors
-  float4* velm;
-  float4* omgm;
+  float4* posm;         // mixed-precision mirrors: cell-relative position
+  float4* velm;         // and velocity relative to the imposed flow
   // neighbour-build scratch
   int* key;             // cell key per particle (old order)
   int* perm;            // new sorted index -> old sorted index

@@ -61,7 +61,9 @@ def test_algorithmic_bytes_per_sphere():
     # the library's own layout: mixed pair 64 + 4 + 4K + 32 + 16 + 48c
     assert bench.layout_bytes("pair", "mixed", K, c, True) == pytest.approx(
         64 + 4 + 4 * K + 32 + 16 + 48 * c)
-    assert bench.layout_bytes("integrate", "mixed", K, c, True) == 328.0
+    # integrator: state 96 + forces 32 + cell and tag 8 read, state 96 +
+    # position and velocity mirrors 48 + cleared forces 32 written
+    assert bench.layout_bytes("integrate", "mixed", K, c, True) == 312.0
 
 
 class _Proc:
