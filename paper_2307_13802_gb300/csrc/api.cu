@@ -805,9 +805,18 @@ int run_steps(susp_t* h, int64_t n_steps, double dt) {
       h->steps_done += m;
       continue;
     }
-    if (graphs_ok && left >= chunk && phase == 0) {
+    // a captured chunk of 32 steps, or for the rest of the call the
+    // largest power of two that is a whole number of sampling periods (each
+    // size captured once and kept)
+    int64_t c = chunk;
+    if (left < chunk) {
+      c = 0;
+      for (int64_t q = 16; q >= 1; q >>= 1)
+        if (q <= left && q % h->p0.sample_every == 0) { c = q; break; }
+    }
+    if (graphs_ok && c > 0 && phase == 0) {
       GraphChunk* g = nullptr;
-      rc = get_graph(h, chunk, dt, &g);
+      rc = get_graph(h, c, dt, &g);
       if (rc) {
         // capture is unavailable: remember why and launch eagerly from now on
         h->graph_err = h->err;
@@ -818,9 +827,9 @@ int run_steps(susp_t* h, int64_t n_steps, double dt) {
       CK(cudaGraphLaunch(g->exec, st));
       h->launches += g->kernels;
       graph_used = true;
-      done += chunk;
-      h->steps_done += chunk;
-      h->graph_steps += chunk;
+      done += c;
+      h->steps_done += c;
+      h->graph_steps += c;
     } else {
       enqueue_steps(h, h->steps_done, left, dt, st, false, nullptr);
       done += left;
