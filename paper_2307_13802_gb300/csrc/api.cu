@@ -678,16 +678,22 @@ bool sampled(const susp_t* h, int64_t step_index) {
 // tensors of the same sample (the two pair-partial buffers alternate with
 // the step); the chunk's last sample is reduced after the closing kick.
 // Either way each accumulator receives the samples in step order.
+// Steps first .. first + n - 1 of a call.  open: the first of them also
+// closes the step before it (the previous chunk of the same call ended
+// without its closing half kick, and its last stress partials are still to
+// be reduced); finish: the last step is closed here and its stress reduced.
+// par: the partial buffer of the first step (the buffers alternate).
 void enqueue_steps(susp_t* h, int64_t first, int64_t n, double dt,
-                   cudaStream_t st, bool capture, std::vector<unsigned long long>* conds) {
+                   cudaStream_t st, bool capture, std::vector<unsigned long long>* conds,
+                   bool open = false, bool finish = true, int par = 0) {
   const bool fused = h->p0.precision == SUSP_MIXED;
   for (int64_t i = 0; i < n; ++i) {
     const int64_t step = first + i;
-    const int close = i > 0 ? 1 : 0;
+    const int close = (i > 0 || open) ? 1 : 0;
     const int skin_prev = close && sampled(h, step - 1);
     const int samp = sampled(h, step);
     StepArgs s = make_args(h, dt, 1, samp);
-    s.ppar = fused ? (int)(i & 1) : 0;
+    s.ppar = fused ? (int)((par + i) & 1) : 0;
     s.fuse_red = fused && skin_prev;
     unsigned long long cond = 0;
     if (capture) {
@@ -742,22 +748,27 @@ void enqueue_steps(susp_t* h, int64_t first, int64_t n, double dt,
     (capture ? h->capture_launches : h->launches) +=
         2 + (h->A.det ? 1 : 0) + ((!fused && (samp || skin_prev)) ? 2 : 0);
   }
+  if (!finish) return;
   StepArgs s = make_args(h, dt, 1, 0);
   const int last_kin = sampled(h, first + n - 1);
   launch_finalize(h, s, last_kin, st);
-  launch_reduce(h, fused ? last_kin : 0, last_kin, fused ? (int)((n - 1) & 1) : 0, st);
+  launch_reduce(h, fused ? last_kin : 0, last_kin, fused ? (int)((par + n - 1) & 1) : 0, st);
   (capture ? h->capture_launches : h->launches) += 1 + (last_kin ? 2 : 0);
 }
 
-int get_graph(susp_t* h, int64_t n, double dt, GraphChunk** out) {
-  auto it = h->graphs.find(n);
+// A captured chunk of n steps in one of its flavours (see enqueue_steps),
+// kept by size and flavour.
+int get_graph(susp_t* h, int64_t n, double dt, bool open, bool finish, int par,
+              GraphChunk** out) {
+  const int64_t key = n * 8 + (open ? 4 : 0) + (finish ? 2 : 0) + (par & 1);
+  auto it = h->graphs.find(key);
   if (it != h->graphs.end()) { *out = &it->second; return SUSP_OK; }
   if (!h->side) CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
   GraphChunk gc;
   std::vector<unsigned long long> conds;
   h->capture_launches = 0;
   CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-  enqueue_steps(h, 0, n, dt, h->stream, true, &conds);
+  enqueue_steps(h, 0, n, dt, h->stream, true, &conds, open, finish, par);
   cudaError_t e = cudaStreamEndCapture(h->stream, &gc.graph);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -770,8 +781,8 @@ int get_graph(susp_t* h, int64_t n, double dt, GraphChunk** out) {
     return fail(h, SUSP_ECUDA, std::string("graph instantiation failed: ") + cudaGetErrorString(e));
   }
   gc.kernels = h->capture_launches;
-  h->graphs[n] = gc;
-  *out = &h->graphs[n];
+  h->graphs[key] = gc;
+  *out = &h->graphs[key];
   return SUSP_OK;
 }
 
@@ -792,6 +803,11 @@ int run_steps(susp_t* h, int64_t n_steps, double dt) {
   const int64_t chunk = 32;
   int64_t done = 0;
   bool graph_used = false;
+  // consecutive chunks of one call run as one sequence of steps: a chunk
+  // after the first closes its predecessor's last step and reduces its
+  // stress, and only the call's last chunk ends with the closing half kick
+  bool open = false;
+  int par = 0;
   while (done < n_steps) {
     const int64_t left = n_steps - done;
     const bool graphs_ok = h->p0.use_graphs && (chunk % h->p0.sample_every == 0);
@@ -800,9 +816,11 @@ int run_steps(susp_t* h, int64_t n_steps, double dt) {
       // eager steps up to the next sampling boundary, where the captured
       // chunks (sampled at their first step) line up again
       const int64_t m = std::min<int64_t>(left, h->p0.sample_every - phase);
-      enqueue_steps(h, h->steps_done, m, dt, st, false, nullptr);
+      enqueue_steps(h, h->steps_done, m, dt, st, false, nullptr, open, done + m == n_steps, par);
       done += m;
       h->steps_done += m;
+      open = true;
+      par = (int)((par + m) & 1);
       continue;
     }
     // a captured chunk of 32 steps, or for the rest of the call the
@@ -816,7 +834,7 @@ int run_steps(susp_t* h, int64_t n_steps, double dt) {
     }
     if (graphs_ok && c > 0 && phase == 0) {
       GraphChunk* g = nullptr;
-      rc = get_graph(h, c, dt, &g);
+      rc = get_graph(h, c, dt, open, done + c == n_steps, par, &g);
       if (rc) {
         // capture is unavailable: remember why and launch eagerly from now on
         h->graph_err = h->err;
@@ -830,8 +848,10 @@ int run_steps(susp_t* h, int64_t n_steps, double dt) {
       done += c;
       h->steps_done += c;
       h->graph_steps += c;
+      open = true;
+      par = (int)((par + c) & 1);
     } else {
-      enqueue_steps(h, h->steps_done, left, dt, st, false, nullptr);
+      enqueue_steps(h, h->steps_done, left, dt, st, false, nullptr, open, true, par);
       done += left;
       h->steps_done += left;
     }

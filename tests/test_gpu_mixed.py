@@ -191,8 +191,9 @@ def test_mixed_viscosity_within_one_percent_of_fp64(susp, record):
 def test_stress_samples_do_not_depend_on_how_steps_are_grouped(susp, sample_every):
     """The mixed path reduces a sampled step's stress inside the next step's
     integrator, and a call's last sample after its closing kick.  70 steps as
-    one call (two 32-step graph replays and an eager tail when every step is
-    sampled, all eager when every third one is) and the same steps as 70
+    one call (captured chunks of 32, 32, 4 and 2 steps run as one sequence
+    when every step is sampled, all eager when every third one is) and the
+    same steps as 70
     one-step calls must put the same samples into the accumulators and the
     series, in the same order.  20,000 spheres make 79 blocks, so a replica
     spans two reduction chunks.  The two runs differ only by the order of the
