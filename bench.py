@@ -48,9 +48,9 @@ NCU_TRAFFIC = {
     # ncu --set full on the 1M bench workload: DRAM read + write per launch / N
     # issue_active: fraction of cycles the kernel issued an instruction (the
     # pair kernel is bound by issue and latency, not by DRAM)
-    "k_pair_mixed": {"bytes_per_sphere": 316.751, "source_sha": "8e17b33fff85e49c",
-                     "issue_active": 0.760, "dram_throughput": 0.220},
-    "k_integrate_mixed": {"bytes_per_sphere": 266.997, "source_sha": "23c8703e3ca7af9c"},
+    "k_pair_mixed": {"bytes_per_sphere": 333.482, "source_sha": "618ef5f2a1baa4a3",
+                     "issue_active": 0.758, "dram_throughput": 0.230},
+    "k_integrate_mixed": {"bytes_per_sphere": 251.151, "source_sha": "dc951ff6aadb9bdb"},
 }
 
 # Double-precision floating-point operations per launch of the FP64 pair
@@ -58,8 +58,8 @@ NCU_TRAFFIC = {
 # DFMA plus 1 per DADD and DMUL (smsp__sass_thread_inst_executed_op_d{fma,add,
 # mul}_pred_on.sum); reported only while the source is unchanged.
 NCU_FP64_FLOPS = {
-    # 497.7 M DADD + 1,190.6 M DFMA + 665.9 M DMUL thread instructions per launch
-    "k_pair_fp64": {"flops_per_sphere": 3544.796, "source_sha": "4235bba8b09978f3"},
+    # 497.7 M DADD + 1,190.9 M DFMA + 666.0 M DMUL thread instructions per launch
+    "k_pair_fp64": {"flops_per_sphere": 3545.513, "source_sha": "bd935770d82aa949"},
 }
 
 
