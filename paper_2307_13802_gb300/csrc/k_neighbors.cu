@@ -233,7 +233,7 @@ __device__ __forceinline__ int wrap_cell(int i, int n) {
   return i < 0 ? i + n : (i >= n ? i - n : i);
 }
 
-__global__ void __launch_bounds__(kBlock) k_build_list(Arrays A, StepArgs s, double rc_fac) {
+__global__ void __launch_bounds__(kBlock, 3) k_build_list(Arrays A, StepArgs s, double rc_fac) {
   if (!gate(A.ctl)) return;
   const int nxt = A.ctl->cur ^ 1;
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -421,14 +421,33 @@ __global__ void __launch_bounds__(kBlock) k_remap_history(Arrays A) {
       if (!(sqrt(d2) < P.w + Q.w)) continue;
     }
     const int oq = A.perm[q];
+    // the pair's slot in the old list: in op's row or in oq's, searched four
+    // entries at a time so that their loads overlap
     int row = -1, slot = -1;
     const int n1 = A.nnb[cur][op];
-    for (int t = 0; t < n1; ++t)
-      if ((A.nbr[cur][(int64_t)t * Np + op] & kNbrIndexMask) == oq) { row = op; slot = t; break; }
-    if (row < 0) {
+    for (int t = 0; t < n1 && slot < 0; t += 4) {
+      int e[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        e[u] = t + u < n1 ? (A.nbr[cur][(int64_t)(t + u) * Np + op] & kNbrIndexMask) : -1;
+#pragma unroll
+      for (int u = 3; u >= 0; --u)
+        if (e[u] == oq) slot = t + u;
+    }
+    if (slot >= 0) {
+      row = op;
+    } else {
       const int n2 = A.nnb[cur][oq];
-      for (int t = 0; t < n2; ++t)
-        if ((A.nbr[cur][(int64_t)t * Np + oq] & kNbrIndexMask) == op) { row = oq; slot = t; break; }
+      for (int t = 0; t < n2 && slot < 0; t += 4) {
+        int e[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          e[u] = t + u < n2 ? (A.nbr[cur][(int64_t)(t + u) * Np + oq] & kNbrIndexMask) : -1;
+#pragma unroll
+        for (int u = 3; u >= 0; --u)
+          if (e[u] == op) slot = t + u;
+      }
+      if (slot >= 0) row = oq;
     }
     if (row < 0) continue;
     if (!((A.cmsk[cur][row] >> slot) & 1ull)) continue;
