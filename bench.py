@@ -38,6 +38,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "bidisperse-1M-phi0.58-pe1000-mu1"
+SMS_GB300 = 152          # streaming multiprocessors of one GB300
+SM_MAX_MHZ = 2070.0      # its maximum SM clock
 METRIC = "particle-steps/s"
 
 # DRAM traffic per launch of the dominant kernel from one ncu capture
@@ -49,7 +51,8 @@ NCU_TRAFFIC = {
     # issue_active: fraction of cycles the kernel issued an instruction (the
     # pair kernel is bound by issue and latency, not by DRAM)
     "k_pair_mixed": {"bytes_per_sphere": 333.482, "source_sha": "618ef5f2a1baa4a3",
-                     "issue_active": 0.758, "dram_throughput": 0.230},
+                     "issue_active": 0.758, "dram_throughput": 0.230,
+                     "warp_instructions_per_sphere": 163.814},
     "k_integrate_mixed": {"bytes_per_sphere": 251.151, "source_sha": "dc951ff6aadb9bdb"},
 }
 
@@ -332,6 +335,18 @@ def run_ours(args, rank, world, local_rank, dist):
                     "contacts_per_sphere": round(c, 3)}
         if ncu:
             roofline["ncu"] = ncu
+        if rec and rec.get("source_sha") == _src_hash(src) and "warp_instructions_per_sphere" in rec:
+            # the instruction-issue roofline of the same launch: warp
+            # instructions (ncu smsp__inst_executed.sum) over the event time,
+            # against one warp instruction per cycle on each of the 4
+            # schedulers of 152 SMs at the SM clock sampled in the timed region
+            sm = SMS_GB300 * 4 * ((clk or {}).get("sm_mhz") or SM_MAX_MHZ) * 1e6
+            inst = rec["warp_instructions_per_sphere"] * N
+            got = inst / (prof[fam]["ms_per_launch"] * 1e-3)
+            roofline["issue"] = {"warp_instructions_per_launch": inst,
+                                 "achieved_ginst_per_s": round(got / 1e9, 1),
+                                 "peak_ginst_per_s": round(sm / 1e9, 1),
+                                 "frac": round(got / sm, 4)}
     rebuild_roof = None
     if prof["rebuild"]["launches"] > 0:
         rb = rebuild_bytes(K) * N
