@@ -40,6 +40,7 @@ struct susp_s {
   int64_t N = 0, Npad = 0;
   std::vector<int64_t> Nr, off;
   std::vector<double> radii, mass, inertia;
+  std::vector<double> sum_a3;   // per replica: sum of a^3 (drag stresslet)
   std::vector<int> rep_of;
   std::vector<Replica> repl_h;
   std::vector<susp_params> pr;
@@ -217,6 +218,7 @@ int common_create(susp_t** out, int32_t R, const int64_t* N_r,
   h->off[0] = 0;
   for (int r = 0; r < R; ++r) h->off[r + 1] = h->off[r] + N_r[r];
   h->radii.assign(radii, radii + N);
+  h->sum_a3.assign(R, 0.0);
   h->mass.resize(N);
   h->inertia.resize(N);
   h->rep_of.resize(N);
@@ -230,6 +232,7 @@ int common_create(susp_t** out, int32_t R, const int64_t* N_r,
         return SUSP_EINVAL;
       }
       h->amax = std::max(h->amax, a);
+      h->sum_a3[r] += a * a * a;
       h->mass[i] = cm * a * a * a;
       h->inertia[i] = 0.4 * h->mass[i] * a * a;
       h->rep_of[i] = r;
@@ -1566,10 +1569,9 @@ int susp_stress(susp_t* h, double* out, int32_t replica) {
   const double np = acc[kAccNp], nk = acc[kAccNk];
   const double V = R.V;
   for (int c = 0; c < kVirLen; ++c) out[c] = np > 0 ? acc[c] / np / V : 0.0;
-  // drag stresslet (20/3) pi eta sum a^3 E / V, E = rate/2 (xy + yx)
-  double s3 = 0.0;
-  for (int64_t i = h->off[replica]; i < h->off[replica + 1]; ++i)
-    s3 += h->radii[i] * h->radii[i] * h->radii[i];
+  // drag stresslet (20/3) pi eta sum a^3 E / V, E = rate/2 (xy + yx); the
+  // sum of a^3 is formed once, at creation
+  const double s3 = h->sum_a3[replica];
   const double dxy = 20.0 / 3.0 * kPi * R.eta * s3 * (0.5 * R.rate) / V;
   for (int c = 0; c < 9; ++c) out[27 + c] = 0.0;
   out[27 + 1] = dxy;
