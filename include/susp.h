@@ -54,7 +54,8 @@ extern "C" {
 #define SUSP_ENOMEM 2    /* device or host allocation failed                */
 #define SUSP_ECUDA 3     /* a CUDA runtime call failed                      */
 #define SUSP_ESTATE 4    /* call order (e.g. step before set_state)         */
-#define SUSP_ENEIGH 5    /* neighbour row exceeded its capacity             */
+#define SUSP_ENEIGH 5    /* neighbour row exceeded its capacity (at 64, or  */
+                         /* inside a call's steps before it could grow)     */
 #define SUSP_EUNSTABLE 6 /* non-finite position/velocity or runaway overlap */
                          /* 7 is not used: no call waits on the device      */
                          /* with a time limit                               */
@@ -92,7 +93,12 @@ typedef struct susp_params {
   int32_t onebody;    /* 1: one-body drag and noise on                      */
   int32_t contact;    /* 1: contact forces on                               */
   int32_t sample_every;/* accumulate the stress every this many steps (>=1) */
-  int32_t kmax;       /* neighbour row capacity (0: default 48)             */
+  int32_t kmax;       /* initial neighbour row capacity (0: default 48);    */
+                      /* it grows, up to 64, before a call whose rebuilds  */
+                      /* could fill it: when a rebuild asked for by the    */
+                      /* host (new state, skin or clock) overflows, and    */
+                      /* when the last build's longest row came within a   */
+                      /* quarter of it                                      */
   int32_t threads_per_particle; /* 0 = autotune, else 1, 2, 4 or 8          */
   int32_t use_graphs; /* 1: replay steps as CUDA graphs (default)           */
   int32_t structural; /* 1: sample the structural Brownian stress (Eq. 26)  */

@@ -82,6 +82,8 @@ struct susp_s {
   int64_t capture_launches = 0;    // kernels in the graph being captured
   int last_nbuilds = 0;
   int last_nbuilds_seen = 0;
+  int last_max_row = 0;            // longest row of the last build seen
+  bool rebuild_pending = false;    // a rebuild the host asked for is still to run
   // profiling: events around each launch, summed per kernel family
   bool profiling = false;
   bool autotuned = false;  // the autotune parameter's one tuning pass is done
@@ -543,6 +545,7 @@ int check_errors(susp_t* h) {
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaGetLastError());
   h->last_nbuilds_seen = c.nbuilds;
+  h->last_max_row = c.max_row;
   if (c.err) {
     int e = c.err;
     int zero = 0;
@@ -557,6 +560,118 @@ int check_errors(susp_t* h) {
     }
     if (e & (kErrNonFinite | kErrWrap)) return fail(h, SUSP_EUNSTABLE, "non-finite positions or velocities");
     return fail(h, SUSP_EUNSTABLE, "unstable state");
+  }
+  return SUSP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// neighbour-row capacity: grown on demand
+// ---------------------------------------------------------------------------
+int rebuild_kernels(const susp_t* h, const StepArgs& s);
+
+// The largest row capacity: the contact bits of a row are one 64-bit word,
+// and the deterministic reverse list holds 32-bit slot indices.
+int kmax_cap(const susp_t* h) {
+  int cap = 64;
+  if (h->p0.deterministic)
+    while (cap > 1 && (int64_t)cap * h->Npad >= ((int64_t)1 << 31)) --cap;
+  return cap;
+}
+
+void dev_free_block(susp_t* h, void* ptr) {
+  auto it = std::find(h->blocks.begin(), h->blocks.end(), ptr);
+  if (it != h->blocks.end()) h->blocks.erase(it);
+  if (h->ufree) h->ufree(ptr, h->uctx);
+  else cudaFree(ptr);
+}
+
+// Row capacity kmax -> knew (> kmax): both copies of the list and the
+// history move to arrays of the new stride with their slots kept (the
+// layouts are slot-major, so a row's first kmax slots keep their places);
+// the deterministic records, rewritten at every evaluation and rebuild, are
+// allocated anew.  The captured graphs hold the old pointers and are dropped.
+// Called between calls (the stream is drained first).
+int grow_kmax(susp_t* h, int knew) {
+  CK(cudaStreamSynchronize(h->stream));
+  Arrays& A = h->A;
+  const int64_t Np = h->Npad;
+  const int64_t So = (int64_t)h->kmax * Np, Sn = (int64_t)knew * Np;
+  std::vector<void*> old;
+  for (int c = 0; c < 2; ++c) {
+    int* nb = nullptr;
+    double* hs = nullptr;
+    if (!alloc_n(h, &nb, Sn) || !alloc_n(h, &hs, (A.mixed ? 4 : 3) * Sn))
+      return fail(h, SUSP_ENOMEM, "out of device memory growing the neighbour rows");
+    CK(cudaMemcpyAsync(nb, A.nbr.a[c], sizeof(int) * So, cudaMemcpyDeviceToDevice, h->stream));
+    if (A.mixed) {
+      CK(cudaMemcpyAsync(hs, A.hist.a[c], sizeof(double) * 4 * So, cudaMemcpyDeviceToDevice,
+                         h->stream));
+    } else {
+      for (int q = 0; q < 3; ++q)
+        CK(cudaMemcpyAsync(hs + q * Sn, A.hist.a[c] + q * So, sizeof(double) * So,
+                           cudaMemcpyDeviceToDevice, h->stream));
+    }
+    old.push_back(A.nbr.a[c]);
+    old.push_back(A.hist.a[c]);
+    A.nbr.a[c] = nb;
+    A.hist.a[c] = hs;
+  }
+  if (A.det) {
+    old.push_back(A.det_slot);
+    old.push_back(A.rev_ent);
+    if (!alloc_n(h, &A.det_slot, 9 * Sn) || !alloc_n(h, &A.rev_ent, Sn))
+      return fail(h, SUSP_ENOMEM, "out of device memory growing the neighbour rows");
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  for (void* ptr : old) dev_free_block(h, ptr);
+  h->kmax = knew;
+  A.kmax = knew;
+  drop_graphs(h);
+  return SUSP_OK;
+}
+
+// A rebuild the host asked for (new state, skin or clock), run on its own
+// with its rows checked: a row above the capacity returns the pre-rebuild
+// state (its copy in the other buffer is untouched by the build), grows the
+// capacity and builds again.  Other errors, and an overflow at the largest
+// capacity, are left for check_errors to report.
+int rebuild_checked(susp_t* h, double dt) {
+  const int mixed = h->p0.precision == SUSP_MIXED;
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    Ctl c0{}, c{};
+    CK(cudaMemcpyAsync(&c0, h->A.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+    const StepArgs s = make_args(h, dt, 0, 0);
+    launch_rebuild(h->A, h->bm, s, h->stream, mixed);
+    h->launches += rebuild_kernels(h, s);
+    CK(cudaMemcpyAsync(&c, h->A.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->last_max_row = c.max_row;
+    if (!(c.err & kErrOverflow) || h->kmax >= kmax_cap(h)) return SUSP_OK;
+    Ctl back = c0;
+    back.err = c.err & ~kErrOverflow;
+    back.need_rebuild = 1;
+    CK(cudaMemcpyAsync(h->A.ctl, &back, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream));
+    const int rc = grow_kmax(h, std::min(kmax_cap(h), std::max(2 * h->kmax, c.max_row + 8)));
+    if (rc) return rc;
+  }
+  return SUSP_OK;
+}
+
+// Before a call's steps: a capacity within a quarter (at least 4) of the
+// last build's longest row grows, so that the builds inside the captured
+// steps, whose rows are only seen when the call ends, keep room; then the
+// rebuild the host asked for, checked.
+int prepare_rows(susp_t* h, double dt) {
+  const int cap = kmax_cap(h);
+  if (h->last_max_row > 0 && h->kmax < cap &&
+      h->last_max_row + std::max(4, h->kmax / 4) > h->kmax) {
+    const int rc = grow_kmax(h, std::min(cap, std::max(2 * h->kmax, h->last_max_row + 8)));
+    if (rc) return rc;
+  }
+  if (h->rebuild_pending) {
+    const int rc = rebuild_checked(h, dt);
+    if (rc) return rc;
+    h->rebuild_pending = false;
   }
   return SUSP_OK;
 }
@@ -797,6 +912,8 @@ int run_steps(susp_t* h, int64_t n_steps, double dt) {
   if (dt != h->last_dt) drop_graphs(h);
   int rc = sync_replicas(h, dt);
   if (rc) return rc;
+  rc = prepare_rows(h, dt);
+  if (rc) return rc;
   h->last_dt = dt;
   cudaStream_t st = h->stream;
   if (!h->forces_valid) {
@@ -948,6 +1065,7 @@ int set_state_impl(susp_t* h, const double* x, const double* U, const double* W,
       h->A, dx, dU, dW, h->d_radius, h->d_mass, h->d_inertia, h->d_rep_of,
                     h->stream);
   launch_request_rebuild(h->A, h->stream);
+  h->rebuild_pending = true;
   h->have_state = true;
   h->forces_valid = false;
   return check_errors(h);
@@ -1303,6 +1421,7 @@ int set_skin_impl(susp_t* h, double skin) {
     CK(cudaMemcpyAsync(h->A.repl, h->repl_h.data(), sizeof(Replica) * h->R,
                        cudaMemcpyHostToDevice, h->stream));
     launch_request_rebuild(h->A, h->stream);
+    h->rebuild_pending = true;
     CK(cudaStreamSynchronize(h->stream));
   }
   return SUSP_OK;
@@ -1431,6 +1550,7 @@ int susp_set_clock(susp_t* h, int64_t k, int32_t replica, double strain) {
   CK(cudaMemcpyAsync(&h->A.ctl->k, &kk, sizeof(long long), cudaMemcpyHostToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   launch_request_rebuild(h->A, h->stream);
+  h->rebuild_pending = true;
   h->forces_valid = false;
   return SUSP_OK;
 }
@@ -1470,6 +1590,8 @@ int susp_evaluate(susp_t* h) {
   CK(cudaSetDevice(h->dev));
   const double dt = h->last_dt;
   int rc = sync_replicas(h, dt);
+  if (rc) return rc;
+  rc = prepare_rows(h, dt);
   if (rc) return rc;
   enqueue_setup_eval(h, dt, 1, h->stream);
   h->forces_valid = true;

@@ -204,3 +204,33 @@ def test_errors_are_reported(susp):
     with pytest.raises(susp.SuspError) as e:
         g3.step(1, 1.0, 1.0, 1e-4, 0)
     assert e.value.code == susp.SUSP_ESTATE
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_row_capacity_grows_and_the_run_is_unchanged(susp, precision, record):
+    # rows of up to ~12 entries at phi = 0.55: a capacity of 6 overflows at
+    # the first build, grows before any step, and the run then follows a
+    # run created with the default capacity (the rows hold the same pairs in
+    # the same order; only the order of the force atomics differs)
+    w = workloads.make(1500, 0.55, 10.0, 1.0, pack_seed=81, dyn_seed=82)
+    p = w.params
+    runs = {}
+    for kmax in (6, 48):
+        g = _gpu_system(susp, w, precision=precision, kmax=kmax)
+        g.set_state(w.x, w.U, w.W)
+        g.step(300, p["shear_rate"], p["kT"], p["dt"], p["seed"])
+        x, _, _ = g.state()
+        F, _ = g.forces()
+        runs[kmax] = (x, F, g.info(), g.history()[0])
+    (xs, Fs, infs, ijs), (xd, Fd, infd, ijd) = runs[6], runs[48]
+    assert infd["max_row"] > 6 and infd["kmax"] == 48
+    assert infs["kmax"] > max(6, infs["max_row"])
+    assert np.array_equal(ijs, ijd)
+    # FP64: atomics order only; mixed: its float atomics, as between a batch
+    # and separate handles (measured on a GB300: FP64 x 1.4e-14, F 4.3e-13;
+    # mixed x 6.5e-9, F 1.1e-7)
+    tx, tf = (1e-12, 1e-11) if precision == "fp64" else (1e-7, 5e-6)
+    record("x", np.abs(xs - xd).max(), tx)
+    record("F", _relerr(Fs, Fd), tf)
+    assert np.abs(xs - xd).max() <= tx
+    assert _relerr(Fs, Fd) <= tf
