@@ -588,8 +588,9 @@ void dev_free_block(susp_t* h, void* ptr) {
 // Row capacity kmax -> knew (> kmax): both copies of the list and the
 // history move to arrays of the new stride with their slots kept (the
 // layouts are slot-major, so a row's first kmax slots keep their places);
-// the deterministic records, rewritten at every evaluation and rebuild, are
-// allocated anew.  The captured graphs hold the old pointers and are dropped.
+// the deterministic reverse list is copied and its pair shares, rewritten at
+// every evaluation, allocated anew.  The captured graphs hold the old
+// pointers and are dropped.
 // Called between calls (the stream is drained first).
 int grow_kmax(susp_t* h, int knew) {
   CK(cudaStreamSynchronize(h->stream));
@@ -617,10 +618,16 @@ int grow_kmax(susp_t* h, int knew) {
     A.hist.a[c] = hs;
   }
   if (A.det) {
+    // the reverse list's entries (slot indices sl * Npad + p, which do not
+    // depend on the capacity) carry over; the pair shares are rewritten at
+    // every evaluation
+    int* re = nullptr;
     old.push_back(A.det_slot);
     old.push_back(A.rev_ent);
-    if (!alloc_n(h, &A.det_slot, 9 * Sn) || !alloc_n(h, &A.rev_ent, Sn))
+    if (!alloc_n(h, &A.det_slot, 9 * Sn) || !alloc_n(h, &re, Sn))
       return fail(h, SUSP_ENOMEM, "out of device memory growing the neighbour rows");
+    CK(cudaMemcpyAsync(re, A.rev_ent, sizeof(int) * So, cudaMemcpyDeviceToDevice, h->stream));
+    A.rev_ent = re;
   }
   CK(cudaStreamSynchronize(h->stream));
   for (void* ptr : old) dev_free_block(h, ptr);

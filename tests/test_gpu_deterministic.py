@@ -149,3 +149,17 @@ def test_mixed_precision_rejects_it(susp):
     with pytest.raises(susp.SuspError) as e:
         susp.System(w.radii, w.box, **_kw(w, precision="mixed", deterministic=1))
     assert e.value.code == susp.SUSP_EINVAL
+
+
+def test_a_grown_row_capacity_gives_the_same_bits(susp):
+    # the capacity grows from 6 at the first build; the rows, and the order
+    # of every deterministic sum, are those of a handle created with 48
+    w = workloads.make(1500, 0.55, 10.0, 1.0, pack_seed=83, dyn_seed=84)
+    out = []
+    for kmax in (6, 48):
+        _, r = _run(susp, w, 300, deterministic=1, kmax=kmax)
+        out.append(r)
+    a, b = out
+    assert a["info"]["kmax"] > 6 and b["info"]["kmax"] == 48
+    for key in ("x", "U", "W", "F", "T", "ij", "xi"):
+        assert np.array_equal(a[key], b[key]), key
