@@ -50,9 +50,9 @@ NCU_TRAFFIC = {
     # ncu --set full on the 1M bench workload: DRAM read + write per launch / N
     # issue_active: fraction of cycles the kernel issued an instruction (the
     # pair kernel is bound by issue and latency, not by DRAM)
-    "k_pair_mixed": {"bytes_per_sphere": 333.482, "source_sha": "618ef5f2a1baa4a3",
-                     "issue_active": 0.758, "dram_throughput": 0.230,
-                     "warp_instructions_per_sphere": 163.814},
+    "k_pair_mixed": {"bytes_per_sphere": 332.638, "source_sha": "0bb6c694e2217c8a",
+                     "issue_active": 0.763, "dram_throughput": 0.234,
+                     "warp_instructions_per_sphere": 162.724},
     "k_integrate_mixed": {"bytes_per_sphere": 251.151, "source_sha": "dc951ff6aadb9bdb"},
 }
 

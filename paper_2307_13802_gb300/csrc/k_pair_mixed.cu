@@ -295,7 +295,9 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
   constexpr int kQ = 64;
   __shared__ int qQ[2][kBlock / 32][kQ];
   __shared__ int qM[2][kBlock / 32][kQ];        // owner lane | slot << 5 | had contact << 12
-  __shared__ float qG[2][kBlock / 32][6][kQ];   // r_x, r_y, r_z, h, S, partner radius
+  // r_x, r_y, r_z, h; the pair kernel forms S = a_p + a_q from the radii, so
+  // that four blocks fit the 164 KB shared-memory carve-out (92 KB of L1)
+  __shared__ float qG[2][kBlock / 32][4][kQ];
   int qn0 = 0, qn1 = 0;
 
   // Pair e of queue qi (1: touching pairs): partner's share by vector
@@ -307,11 +309,13 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
     const int meta = qM[qi][warp][e];
     const int o = meta & 31, sl = (meta >> 5) & 127;
     const float rpq[3] = {qG[qi][warp][0][e], qG[qi][warp][1][e], qG[qi][warp][2][e]};
-    const float h = qG[qi][warp][3][e], S = qG[qi][warp][4][e], aq = qG[qi][warp][5][e];
-    const float d = S + h;
-    const float xi = 2.0f * h / S;
+    const float h = qG[qi][warp][3][e];
     const int po = pb + warp * 32 + o;
     const float ap = sA[tid - lane + o];
+    const float aq = __ldg(PM + 2 * q).w;
+    const float S = ap + aq;
+    const float d = S + h;
+    const float xi = 2.0f * h / S;
     const float4 WPo = __ldg(OMD + 2 * po), WQ = __ldg(OMD + 2 * q);
     const float4 VPo = __ldg(VM + po), VQ = __ldg(VM + q);
     const int tp = __float_as_int(VPo.w), tq = __float_as_int(VQ.w);
@@ -521,7 +525,7 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
       if (base + 32 < total) locate(base + 32);
       bool keep = false, touch = false;
       float wst = 0.0f, dst = 1.0f, rst[3] = {0.f, 0.f, 0.f};
-      float gq[6];
+      float gq[4];
       if (t < total) {
         const int po = pb + warp * 32 + o;
         const int q = qe & kNbrIndexMask;
@@ -595,7 +599,7 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
             keep = true;
             touch = s.contact && h < 0.0f;
             gq[0] = rh[0]; gq[1] = rh[1]; gq[2] = rh[2];
-            gq[3] = h; gq[4] = Sh; gq[5] = Q.w;
+            gq[3] = h;
           }
         }
       }
@@ -621,7 +625,7 @@ k_pair_mixed(Arrays A, BlockMap bm, StepArgs s) {
         qQ[qk][warp][e] = qe & kNbrIndexMask;
         qM[qk][warp][e] = o | (sl << 5) | ((FRIC && ((ocm >> sl) & 1ull)) ? (1 << 12) : 0);
 #pragma unroll
-        for (int c6 = 0; c6 < 6; ++c6) qG[qk][warp][c6][e] = gq[c6];
+        for (int c6 = 0; c6 < 4; ++c6) qG[qk][warp][c6][e] = gq[c6];
       }
       qn0 += __popc(m0);
       qn1 += __popc(m1);
