@@ -117,7 +117,7 @@ typedef struct susp_params {
                       /* (SUSP_FP64 only, kmax * N < 2^31): each pair's     */
                       /* shares go to its own slot and every sphere sums    */
                       /* them in a fixed order, so repeated runs are        */
-                      /* bitwise equal (a step costs about 3% more at 1M    */
+                      /* bitwise equal (a step costs about 4% more at 1M    */
                       /* spheres; the reverse list takes 4 B per slot and  */
                       /* the shares 72 B per slot).                         */
                       /* The stress reductions are always in a fixed order  */
