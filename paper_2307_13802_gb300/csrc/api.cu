@@ -597,36 +597,48 @@ int grow_kmax(susp_t* h, int knew) {
   Arrays& A = h->A;
   const int64_t Np = h->Npad;
   const int64_t So = (int64_t)h->kmax * Np, Sn = (int64_t)knew * Np;
+  // every new array first, so that a failed allocation leaves the handle as
+  // it was
+  int* nb[2] = {nullptr, nullptr};
+  double* hs[2] = {nullptr, nullptr};
+  double* ds = nullptr;
+  int* re = nullptr;
+  bool ok = true;
+  for (int c = 0; c < 2; ++c) {
+    ok = ok && alloc_n(h, &nb[c], Sn);
+    ok = ok && alloc_n(h, &hs[c], (A.mixed ? 4 : 3) * Sn);
+  }
+  if (A.det) ok = ok && alloc_n(h, &ds, 9 * Sn) && alloc_n(h, &re, Sn);
+  if (!ok) {
+    for (void* ptr : {(void*)nb[0], (void*)nb[1], (void*)hs[0], (void*)hs[1], (void*)ds, (void*)re})
+      if (ptr) dev_free_block(h, ptr);
+    return fail(h, SUSP_ENOMEM, "out of device memory growing the neighbour rows");
+  }
   std::vector<void*> old;
   for (int c = 0; c < 2; ++c) {
-    int* nb = nullptr;
-    double* hs = nullptr;
-    if (!alloc_n(h, &nb, Sn) || !alloc_n(h, &hs, (A.mixed ? 4 : 3) * Sn))
-      return fail(h, SUSP_ENOMEM, "out of device memory growing the neighbour rows");
-    CK(cudaMemcpyAsync(nb, A.nbr.a[c], sizeof(int) * So, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(nb[c], A.nbr.a[c], sizeof(int) * So, cudaMemcpyDeviceToDevice,
+                       h->stream));
     if (A.mixed) {
-      CK(cudaMemcpyAsync(hs, A.hist.a[c], sizeof(double) * 4 * So, cudaMemcpyDeviceToDevice,
+      CK(cudaMemcpyAsync(hs[c], A.hist.a[c], sizeof(double) * 4 * So, cudaMemcpyDeviceToDevice,
                          h->stream));
     } else {
       for (int q = 0; q < 3; ++q)
-        CK(cudaMemcpyAsync(hs + q * Sn, A.hist.a[c] + q * So, sizeof(double) * So,
+        CK(cudaMemcpyAsync(hs[c] + q * Sn, A.hist.a[c] + q * So, sizeof(double) * So,
                            cudaMemcpyDeviceToDevice, h->stream));
     }
     old.push_back(A.nbr.a[c]);
     old.push_back(A.hist.a[c]);
-    A.nbr.a[c] = nb;
-    A.hist.a[c] = hs;
+    A.nbr.a[c] = nb[c];
+    A.hist.a[c] = hs[c];
   }
   if (A.det) {
     // the reverse list's entries (slot indices sl * Npad + p, which do not
     // depend on the capacity) carry over; the pair shares are rewritten at
     // every evaluation
-    int* re = nullptr;
+    CK(cudaMemcpyAsync(re, A.rev_ent, sizeof(int) * So, cudaMemcpyDeviceToDevice, h->stream));
     old.push_back(A.det_slot);
     old.push_back(A.rev_ent);
-    if (!alloc_n(h, &A.det_slot, 9 * Sn) || !alloc_n(h, &re, Sn))
-      return fail(h, SUSP_ENOMEM, "out of device memory growing the neighbour rows");
-    CK(cudaMemcpyAsync(re, A.rev_ent, sizeof(int) * So, cudaMemcpyDeviceToDevice, h->stream));
+    A.det_slot = ds;
     A.rev_ent = re;
   }
   CK(cudaStreamSynchronize(h->stream));
@@ -659,7 +671,14 @@ int rebuild_checked(susp_t* h, double dt) {
     back.need_rebuild = 1;
     CK(cudaMemcpyAsync(h->A.ctl, &back, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream));
     const int rc = grow_kmax(h, std::min(kmax_cap(h), std::max(2 * h->kmax, c.max_row + 8)));
-    if (rc) return rc;
+    if (rc) {
+      // no room to grow: build again at the old capacity, so that the
+      // arrays the build keeps once (cells, tag map, mirrors) match the state
+      launch_rebuild(h->A, h->bm, s, h->stream, mixed);
+      h->launches += rebuild_kernels(h, s);
+      cudaStreamSynchronize(h->stream);
+      return rc;
+    }
   }
   return SUSP_OK;
 }
